@@ -1,0 +1,164 @@
+/*
+ * flgf.h -- C ABI of the GB300 (sm_103a) multi-resolution fast lattice
+ * Green's function solver (Dorschner, Yu, Mengaldo & Colonius,
+ * arXiv:1911.10228).
+ *
+ * Problem (Sec. 2, the discrete Poisson equation and Eq. discretConv):
+ *     L_Q u(n) = f(n),  supp f in Omega_h,   u(n) = sum_m G(n - m) f(m),
+ * with L_Q the 7-point Laplacian (sum of the 6 face neighbours minus 6 u)
+ * and G its lattice Green's function on the unbounded lattice.  On a level
+ * with spacing h the library returns u = h^2 (G * f), i.e. it solves
+ * L_Q^{(h)} u = (7-point stencil)/h^2 u = f.
+ *
+ * Mesh (Sec. 2.1 and Sec. 3): a problem is a set of refinement levels
+ * l = 0..L-1 (0 = coarsest, spacing h_l = h0 / 2^l).  Each level is a set of
+ * cubic blocks of N^3 cells; block (c0, c1, c2) of level l covers cells
+ * c*N .. c*N + N - 1 of that level's lattice on every axis.  Block c of level
+ * l is refined ("non-leaf") when all 8 blocks 2c + {0,1}^3 exist on level
+ * l+1; partial refinement is rejected.  Every non-leaf block must have its 26
+ * same-level neighbours (the one-block buffer of Sec. 3, "Regularization and
+ * Interpolation operators").  The answer is u on the leaf blocks of every
+ * level; on non-leaf blocks the returned values are the field of the leaf
+ * sources only (an intermediate of the scheme).
+ *
+ * Method: per level, the FLGF of Sec. 2.1 (octree of blocks, near field at
+ * the finest octree level, influence lists, Lagrange interpolation with n_I
+ * nodes, block-wise zero-padded (2N)^3 FFT convolution); across levels the
+ * scheme of Sec. 3 (coarsening, two-FMM leaf/non-leaf subtraction,
+ * accumulation with quadratic coarse-fine interpolation, source correction).
+ *
+ * Data layout: block values are arrays [nblk][N][N][N], C order (the last
+ * index along axis 2 is fastest), in the order the blocks were given.
+ * Values are double for FLGF_FP64 contexts and float for FLGF_FP32.
+ *
+ * Ownership: the library allocates and owns all device memory of a context
+ * and a block set (allocation happens only in the *_create calls).  Pointers
+ * passed in are borrowed for the duration of the call.  All GPU work is
+ * enqueued on the context's stream; calls that read results into host memory
+ * synchronise that stream.  A handle must not be used from two threads at
+ * once; distinct handles are independent.
+ *
+ * Errors: every int-returning call returns FLGF_OK (0) or a negative FLGF_E*
+ * code and never throws; flgf_last_error() describes the last failure of the
+ * context.  A CUDA failure reports FLGF_ECUDA and may leave the context's
+ * stream in an error state.
+ */
+#ifndef FLGF_H
+#define FLGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FLGF_OK = 0,
+  FLGF_EINVAL = -1,   /* bad argument (sizes, indices, precision, option) */
+  FLGF_ENOMEM = -2,   /* device or host allocation failed */
+  FLGF_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+  FLGF_EMESH = -4,    /* block set violates the mesh rules (duplicates, partial refinement, buffer) */
+  FLGF_ESTATE = -5,   /* call out of order (e.g. potential before solve) */
+  FLGF_EDEVICE = -6   /* a kernel reported an error status (e.g. a missing halo block) */
+};
+
+enum { FLGF_FP64 = 0, FLGF_FP32 = 1 };  /* arithmetic and storage precision of a context */
+enum { FLGF_HOST = 0, FLGF_DEVICE = 1 }; /* where a caller buffer lives */
+
+typedef struct flgf_opts {
+  int N;               /* block side, 8 or 16 (Sec. 2.1: blocks of N_b = n_b^3 cells) */
+  int n_interp;        /* Lagrange interpolation nodes n_I, 2..min(N, 10) (Sec. 2.1) */
+  int precision;       /* FLGF_FP64 or FLGF_FP32; LGF generation is always FP64 */
+  int max_oct_levels;  /* octree levels whose kernel spectra are cached (1..8, default 6) */
+  int table_radius;    /* LGF quadrature table radius, default 100 (Sec. 2) */
+  int asym_radius;     /* A^3 up to this radius, A^2 beyond, default 600 (Sec. 2) */
+  void* stream;        /* cudaStream_t for all work; NULL = the legacy default stream */
+} flgf_opts;
+
+typedef struct flgf_ctx flgf_ctx;
+typedef struct flgf_blockset flgf_blockset;
+
+/* Fill opts with the defaults above (N = 16, n_I = 6, FP64). */
+void flgf_default_opts(flgf_opts* o);
+
+/* Create a context: generates the FP64 LGF table by quadrature of Eq. GL_B
+ * (|n| <= table_radius), the far-field switch (A^3, A^2; Sec. 2) and the
+ * kernel spectra of every relative block offset in [-3, 3]^3 for octree
+ * levels 0..max_oct_levels-1 (R2C FFT of the (2N)^3 kernel array
+ * G(2^k (N d + Delta))).  Synchronises the stream.  *out is NULL on failure. */
+int flgf_create(flgf_ctx** out, const flgf_opts* o);
+void flgf_destroy(flgf_ctx* ctx);
+/* Message of the last failure on this context (never NULL; "" if none). */
+const char* flgf_last_error(const flgf_ctx* ctx);
+
+/* G(n) at n_pts integer points pts[3*i..3*i+2] as the library evaluates it
+ * (table / A^3 / A^2), written to host memory out[n_pts].  Synchronises. */
+int flgf_lgf_eval(flgf_ctx* ctx, int n_pts, const int32_t* pts, double* out);
+
+/* Kernel spectrum of octree level k and block offset d = (d0, d1, d2) in
+ * [-3, 3]^3, in natural order [k0 < 2N][k1 < 2N][k2 <= N] as interleaved
+ * (re, im) doubles written to host memory out[2 * 4N^2(N+1)].  In FP32
+ * contexts the stored single-precision values are widened.  Synchronises. */
+int flgf_kernel_spectrum(flgf_ctx* ctx, int k, int d0, int d1, int d2, double* out);
+
+/* Create a block set holding n_problems independent problems (1 for a plain
+ * solve; several for the batched form, which runs every stage of all problems
+ * in the same kernel launches).
+ *   n_levels[p]              refinement levels of problem p (>= 1)
+ *   nblk[q]                  blocks per level, concatenated over problems and levels
+ *   coords[3*i..]            block coordinates, concatenated in the same order
+ *   h0[p]                    spacing of level 0 of problem p (> 0)
+ * Validates the mesh (FLGF_EMESH with a message on violation), builds each
+ * level's octree, near/influence lists and launch tiles, and allocates all
+ * device buffers. */
+int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
+                         const int32_t* coords, const double* h0, flgf_blockset** out);
+void flgf_blockset_destroy(flgf_blockset* bs);
+
+/* Total leaf cells (degrees of freedom of the composite mesh) over all problems. */
+int64_t flgf_blockset_dof(const flgf_blockset* bs);
+
+/* Copy the source of (problem, level) from f ([nblk][N][N][N], context
+ * precision).  Values on non-leaf blocks are ignored (they are replaced by the
+ * coarsened finer source, Sec. 3 step 1). */
+int flgf_load_source(flgf_blockset* bs, int problem, int level, const void* f, int where);
+
+/* Solve every problem of the block set (Sec. 3 algorithm; with one level it is
+ * the FLGF of Sec. 2.1).  Enqueued on the context stream, no synchronisation. */
+int flgf_solve(flgf_blockset* bs);
+
+/* Copy u of (problem, level) into u ([nblk][N][N][N]); synchronises for HOST. */
+int flgf_get_potential(flgf_blockset* bs, int problem, int level, void* u, int where);
+
+/* out = L_Q^{(h_l)} u on the blocks of (problem, level), using same-level face
+ * neighbours; cells with a missing neighbour get 0 (Sec. 3.1's consistency
+ * check omega_h = L_Q Psi_h).  u and out: [nblk][N][N][N]. */
+int flgf_laplacian(flgf_blockset* bs, int problem, int level, const void* u, void* out, int where);
+
+/* Options of a block set. */
+enum {
+  FLGF_OPT_CORRECTION = 1,  /* 1 (default): source correction of Sec. 3 on; 0: off */
+  FLGF_OPT_GRAPH = 2,       /* 1: capture the solve's launch sequence in a CUDA graph on first use */
+  FLGF_OPT_TIMING = 3       /* 1: record CUDA events between stages (see flgf_stage_times) */
+};
+int flgf_set_option(flgf_blockset* bs, int key, int value);
+
+/* Stage times in ms accumulated over the solves run with FLGF_OPT_TIMING = 1
+ * since the last reset, and the number of solves.  Stages:
+ * 0 coarsen, 1 anterpolation, 2 forward FFT, 3 spectrum MAC, 4 inverse FFT,
+ * 5 interpolation, 6 multi-resolution coupling (select, J^l, correction).
+ * n_stages <= 7.  reset != 0 zeroes the accumulators afterwards. */
+int flgf_stage_times(flgf_blockset* bs, double* ms, int n_stages, int* n_solves, int reset);
+
+/* Work of one solve for roofline accounting: the number of (target, source)
+ * block pairs of the spectrum MAC, of forward and inverse FFTs and of cached
+ * kernel-spectrum offsets it touches. */
+int flgf_work_counts(const flgf_blockset* bs, int64_t* pairs, int64_t* fwd_ffts, int64_t* inv_ffts,
+                     int64_t* kernel_offsets);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLGF_H */

@@ -60,17 +60,29 @@ class Level:
         self.N = N
         self.index = {tuple(int(v) for v in c): i for i, c in enumerate(self.coords)}
 
-    def cell_values(self, field, cells):
-        """field values at global cell coordinates (..., 3); KeyError if absent."""
+    def block_ids(self, blk):
+        """Indices of blocks (M, 3); -1 where absent."""
+        blk = np.asarray(blk, dtype=np.int64).reshape(-1, 3)
+        uniq, inv = np.unique(blk, axis=0, return_inverse=True)
+        ids = np.array([self.index.get(tuple(int(v) for v in u), -1) for u in uniq], dtype=np.int64)
+        return ids[inv.ravel()]
+
+    def cell_values(self, field, cells, missing_ok: bool = False):
+        """field values at global cell coordinates (..., 3); KeyError if absent
+        (or 0 and a False mask entry with missing_ok)."""
         N = self.N
         cells = np.asarray(cells, dtype=np.int64)
         flat = cells.reshape(-1, 3)
         blk = flat // N
         loc = flat - blk * N
-        out = np.empty(flat.shape[0])
-        for r in range(flat.shape[0]):
-            b = self.index[tuple(int(v) for v in blk[r])]
-            out[r] = field[b, loc[r, 0], loc[r, 1], loc[r, 2]]
+        b = self.block_ids(blk)
+        have = b >= 0
+        if not missing_ok and not np.all(have):
+            raise KeyError("cell outside the level's blocks")
+        out = np.zeros(flat.shape[0])
+        out[have] = field[b[have], loc[have, 0], loc[have, 1], loc[have, 2]]
+        if missing_ok:
+            return out.reshape(cells.shape[:-1]), have.reshape(cells.shape[:-1])
         return out.reshape(cells.shape[:-1])
 
 
@@ -140,19 +152,9 @@ def laplacian_on_level(level: Level, u, h: float):
         acc = -6.0 * u[b]
         ok = np.ones((N, N, N), dtype=bool)
         for o in off:
-            nb = cells + o
-            blk = nb // N
-            flat_blk = blk.reshape(-1, 3)
-            loc = (nb - blk * N).reshape(-1, 3)
-            vals = np.zeros(flat_blk.shape[0])
-            have = np.zeros(flat_blk.shape[0], dtype=bool)
-            for r in range(flat_blk.shape[0]):
-                j = level.index.get(tuple(int(v) for v in flat_blk[r]))
-                if j is not None:
-                    vals[r] = u[j, loc[r, 0], loc[r, 1], loc[r, 2]]
-                    have[r] = True
-            acc = acc + vals.reshape(N, N, N)
-            ok &= have.reshape(N, N, N)
+            vals, have = level.cell_values(u, cells + o, missing_ok=True)
+            acc = acc + vals
+            ok &= have
         out[b] = np.where(ok, acc / (h * h), 0.0)
         mask[b] = ok
     return out, mask

@@ -1,0 +1,397 @@
+// a2 / a4: zero-padded (2N)^3 block FFTs for the block-wise convolution (Sec. 2.1).
+//
+// A source block holds N^3 values; the circular convolution of size 2N per
+// axis with the (2N)^3 kernel array equals the linear one on the block
+// (2N - 1 <= 2N points), so each block is zero-padded to (2N)^3, transformed
+// with a real-to-complex FFT, multiplied with kernel spectra, and transformed
+// back; only the first N^3 outputs are kept.
+//
+// Design (one CTA per block, whole 3-D transform in shared memory):
+//   forward:  axis 2 (real, N nonzero of 2N) -> axis 1 -> axis 0, the last
+//             pass written straight from registers into the chunked spectrum
+//             layout in HBM.  Shared memory holds [N][2N][N+1] complex (the
+//             axis-0 half that is nonzero before the last pass).
+//   inverse:  axis 0 (only N outputs kept) -> axis 1 -> axis 2 (complex to
+//             real, N outputs kept), reading the chunked spectrum layout.
+// Each thread owns a whole line and transforms it in registers with a fully
+// unrolled radix-2 FFT; the zero half of the input (forward) or the unused
+// half of the output (inverse) is pruned by splitting the first (last)
+// butterfly stage into two half-length transforms.
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace flgf {
+
+// e^{-2 pi i j / 32}, j = 0..31, filled once from the host.
+__constant__ double c_twd[32][2];
+__constant__ float c_twf[32][2];
+
+cudaError_t fft_init_constants() {
+  double td[32][2];
+  float tf[32][2];
+  for (int j = 0; j < 32; ++j) {
+    const long double a = -2.0L * 3.141592653589793238462643383279502884L * j / 32.0L;
+    td[j][0] = (double)cosl(a);
+    td[j][1] = (double)sinl(a);
+    tf[j][0] = (float)td[j][0];
+    tf[j][1] = (float)td[j][1];
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_twd, td, sizeof(td));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_twf, tf, sizeof(tf));
+}
+
+template <typename R> __device__ __forceinline__ R tw_re(int j);
+template <typename R> __device__ __forceinline__ R tw_im(int j);
+template <> __device__ __forceinline__ double tw_re<double>(int j) { return c_twd[j][0]; }
+template <> __device__ __forceinline__ double tw_im<double>(int j) { return c_twd[j][1]; }
+template <> __device__ __forceinline__ float tw_re<float>(int j) { return c_twf[j][0]; }
+template <> __device__ __forceinline__ float tw_im<float>(int j) { return c_twf[j][1]; }
+
+// In-register radix-2 FFT of length L (<= 32), natural order in and out.
+// DIR = -1: forward (e^{-2 pi i jk/L}); DIR = +1: inverse without
+// normalisation.  Recursive even/odd split: every array index is a
+// compile-time constant, so the arrays live in registers.
+template <int L, int DIR, typename R>
+struct RegFFT {
+  static __device__ __forceinline__ void run(R* re, R* im) {
+    constexpr int H = L / 2;
+    R er[H], ei[H], odr[H], odi[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      er[j] = re[2 * j]; ei[j] = im[2 * j];
+      odr[j] = re[2 * j + 1]; odi[j] = im[2 * j + 1];
+    }
+    RegFFT<H, DIR, R>::run(er, ei);
+    RegFFT<H, DIR, R>::run(odr, odi);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      R tr, ti;
+      if (k == 0) {
+        tr = odr[k]; ti = odi[k];
+      } else if (4 * k == L) {  // w = -i (forward) or +i (inverse)
+        tr = DIR < 0 ? odi[k] : -odi[k];
+        ti = DIR < 0 ? -odr[k] : odr[k];
+      } else {
+        const R wr = tw_re<R>(k * (32 / L));
+        const R wi = DIR < 0 ? tw_im<R>(k * (32 / L)) : -tw_im<R>(k * (32 / L));
+        tr = wr * odr[k] - wi * odi[k];
+        ti = wr * odi[k] + wi * odr[k];
+      }
+      re[k] = er[k] + tr; im[k] = ei[k] + ti;
+      re[k + H] = er[k] - tr; im[k + H] = ei[k] - ti;
+    }
+  }
+};
+template <int DIR, typename R>
+struct RegFFT<1, DIR, R> {
+  static __device__ __forceinline__ void run(R*, R*) {}
+};
+template <int DIR, typename R>
+struct RegFFT<2, DIR, R> {
+  static __device__ __forceinline__ void run(R* re, R* im) {
+    const R ar = re[0], ai = im[0];
+    re[0] = ar + re[1]; im[0] = ai + im[1];
+    re[1] = ar - re[1]; im[1] = ai - im[1];
+  }
+};
+
+template <int L, int DIR, typename R>
+__device__ __forceinline__ void fft_reg(R* re, R* im) {
+  RegFFT<L, DIR, R>::run(re, im);
+}
+
+// Forward FFT of length L whose inputs L/2..L-1 are zero.  out(k, re, im) is
+// called for every k = 0..L-1 (even k first).
+template <int L, typename R, typename Out>
+__device__ __forceinline__ void fft_fwd_pruned(const R* xr, const R* xi, Out out) {
+  constexpr int H = L / 2;
+  R ar[H], ai[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) { ar[j] = xr[j]; ai[j] = xi[j]; }
+  fft_reg<H, -1>(ar, ai);
+#pragma unroll
+  for (int m = 0; m < H; ++m) out(2 * m, ar[m], ai[m]);
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    if (j == 0) { ar[j] = xr[j]; ai[j] = xi[j]; continue; }
+    const R wr = tw_re<R>(j * (32 / L)), wi = tw_im<R>(j * (32 / L));
+    ar[j] = xr[j] * wr - xi[j] * wi;
+    ai[j] = xr[j] * wi + xi[j] * wr;
+  }
+  fft_reg<H, -1>(ar, ai);
+#pragma unroll
+  for (int m = 0; m < H; ++m) out(2 * m + 1, ar[m], ai[m]);
+}
+
+// Inverse FFT (no normalisation) of length L, only outputs 0..L/2-1.
+template <int L, typename R>
+__device__ __forceinline__ void fft_inv_pruned(const R* Xr, const R* Xi, R* xr, R* xi) {
+  constexpr int H = L / 2;
+  R er[H], ei[H], odr[H], odi[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    er[m] = Xr[2 * m]; ei[m] = Xi[2 * m];
+    odr[m] = Xr[2 * m + 1]; odi[m] = Xi[2 * m + 1];
+  }
+  fft_reg<H, +1>(er, ei);
+  fft_reg<H, +1>(odr, odi);
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    if (j == 0) { xr[j] = er[j] + odr[j]; xi[j] = ei[j] + odi[j]; continue; }
+    const R wr = tw_re<R>(j * (32 / L)), wi = -tw_im<R>(j * (32 / L));
+    xr[j] = er[j] + (odr[j] * wr - odi[j] * wi);
+    xi[j] = ei[j] + (odr[j] * wi + odi[j] * wr);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward transform of source blocks.
+// ---------------------------------------------------------------------------
+template <typename R, int N>
+__global__ void __launch_bounds__(N * N) fft_fwd_kernel(const R* __restrict__ nodes, const int* __restrict__ gids,
+                                                        const int* __restrict__ sids, cplx<R>* __restrict__ spec,
+                                                        int spec_blocks) {
+  constexpr int P = 2 * N, NX = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* buf = reinterpret_cast<cplx<R>*>(smem_raw);  // [N z][P y][NX kx]
+  const int gid = gids[blockIdx.x], sid = sids[blockIdx.x];
+  const R* in = nodes + (size_t)gid * N * N * N;
+  const int tid = threadIdx.x;
+
+  // axis 2 (real input, N of 2N nonzero)
+  for (int line = tid; line < N * N; line += blockDim.x) {
+    const int z = line / N, y = line % N;
+    R xr[N], xi[N];
+#pragma unroll
+    for (int x = 0; x < N; ++x) { xr[x] = in[(z * N + y) * N + x]; xi[x] = R(0); }
+    cplx<R>* row = buf + (z * P + y) * NX;
+    fft_fwd_pruned<P>(xr, xi, [&](int k, R re, R im) {
+      if (k <= N) row[k] = cplx<R>{re, im};
+    });
+  }
+  __syncthreads();
+  // axis 1 (N of 2N nonzero)
+  for (int line = tid; line < N * NX; line += blockDim.x) {
+    const int z = line / NX, kx = line % NX;
+    R xr[N], xi[N];
+#pragma unroll
+    for (int y = 0; y < N; ++y) {
+      const cplx<R> v = buf[(z * P + y) * NX + kx];
+      xr[y] = v.re; xi[y] = v.im;
+    }
+    fft_fwd_pruned<P>(xr, xi, [&](int k, R re, R im) { buf[(z * P + k) * NX + kx] = cplx<R>{re, im}; });
+  }
+  __syncthreads();
+  // axis 0 (N of 2N nonzero) -> HBM, chunked layout
+  for (int line = tid; line < P * NX; line += blockDim.x) {
+    const int ky = line / NX, kx = line % NX;
+    R xr[N], xi[N];
+#pragma unroll
+    for (int z = 0; z < N; ++z) {
+      const cplx<R> v = buf[(z * P + ky) * NX + kx];
+      xr[z] = v.re; xi[z] = v.im;
+    }
+    fft_fwd_pruned<P>(xr, xi, [&](int k, R re, R im) {
+      const int w = (k * P + ky) * NX + kx;
+      spec[spec_index<R>(w, sid, spec_blocks)] = cplx<R>{re, im};
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse transform of accumulated spectra; keeps the first N^3 outputs.
+// ---------------------------------------------------------------------------
+template <typename R, int N>
+__global__ void __launch_bounds__(N * N) fft_inv_kernel(const cplx<R>* __restrict__ acc, int spec_blocks,
+                                                        const int* __restrict__ sids, const int* __restrict__ gids,
+                                                        const double* __restrict__ scales, R* __restrict__ out) {
+  constexpr int P = 2 * N, NX = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* buf = reinterpret_cast<cplx<R>*>(smem_raw);  // [N z][P y][NX kx]
+  const int sid = sids[blockIdx.x], gid = gids[blockIdx.x];
+  const int tid = threadIdx.x;
+
+  // axis 0: 2N inputs from HBM, keep z < N
+  for (int line = tid; line < P * NX; line += blockDim.x) {
+    const int ky = line / NX, kx = line % NX;
+    R Xr[P], Xi[P];
+#pragma unroll
+    for (int kz = 0; kz < P; ++kz) {
+      const cplx<R> v = acc[spec_index<R>((kz * P + ky) * NX + kx, sid, spec_blocks)];
+      Xr[kz] = v.re; Xi[kz] = v.im;
+    }
+    R xr[N], xi[N];
+    fft_inv_pruned<P>(Xr, Xi, xr, xi);
+#pragma unroll
+    for (int z = 0; z < N; ++z) buf[(z * P + ky) * NX + kx] = cplx<R>{xr[z], xi[z]};
+  }
+  __syncthreads();
+  // axis 1: keep y < N
+  for (int line = tid; line < N * NX; line += blockDim.x) {
+    const int z = line / NX, kx = line % NX;
+    R Xr[P], Xi[P];
+#pragma unroll
+    for (int ky = 0; ky < P; ++ky) {
+      const cplx<R> v = buf[(z * P + ky) * NX + kx];
+      Xr[ky] = v.re; Xi[ky] = v.im;
+    }
+    R xr[N], xi[N];
+    fft_inv_pruned<P>(Xr, Xi, xr, xi);
+#pragma unroll
+    for (int y = 0; y < N; ++y) buf[(z * P + y) * NX + kx] = cplx<R>{xr[y], xi[y]};
+  }
+  __syncthreads();
+  // axis 2: Hermitian half -> real, keep x < N
+  const R scale = (R)(scales[blockIdx.x] / (double)(P * P * P));
+  R* o = out + (size_t)gid * N * N * N;
+  for (int line = tid; line < N * N; line += blockDim.x) {
+    const int z = line / N, y = line % N;
+    const cplx<R>* row = buf + (z * P + y) * NX;
+    R Xr[P], Xi[P];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) { const cplx<R> v = row[k]; Xr[k] = v.re; Xi[k] = v.im; }
+#pragma unroll
+    for (int k = N + 1; k < P; ++k) { Xr[k] = Xr[P - k]; Xi[k] = -Xi[P - k]; }
+    R xr[N], xi[N];
+    fft_inv_pruned<P>(Xr, Xi, xr, xi);
+#pragma unroll
+    for (int x = 0; x < N; ++x) o[(z * N + y) * N + x] = scale * xr[x];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel spectra (setup, FP64): full 2N along axes 2 and 1, the 2N axis-0
+// planes split into two halves of N that are transformed as pruned inputs
+// and combined as LO + (-1)^{k0} HI.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(N * N) fft_kernel_half(const double* __restrict__ karr, int zoff,
+                                                         cplx<double>* __restrict__ out) {
+  constexpr int P = 2 * N, NX = N + 1, NW = P * P * NX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<double>* buf = reinterpret_cast<cplx<double>*>(smem_raw);  // [N z][P y][NX kx]
+  const int d = blockIdx.x;
+  const double* in = karr + (size_t)d * P * P * P;
+  const int tid = threadIdx.x;
+  for (int line = tid; line < N * P; line += blockDim.x) {
+    const int z = line / P, y = line % P;
+    double xr[P], xi[P];
+#pragma unroll
+    for (int x = 0; x < P; ++x) { xr[x] = in[((z + zoff) * P + y) * P + x]; xi[x] = 0.0; }
+    fft_reg<P, -1>(xr, xi);
+#pragma unroll
+    for (int k = 0; k <= N; ++k) buf[(z * P + y) * NX + k] = cplx<double>{xr[k], xi[k]};
+  }
+  __syncthreads();
+  for (int line = tid; line < N * NX; line += blockDim.x) {
+    const int z = line / NX, kx = line % NX;
+    double xr[P], xi[P];
+#pragma unroll
+    for (int y = 0; y < P; ++y) { const cplx<double> v = buf[(z * P + y) * NX + kx]; xr[y] = v.re; xi[y] = v.im; }
+    fft_reg<P, -1>(xr, xi);
+#pragma unroll
+    for (int y = 0; y < P; ++y) buf[(z * P + y) * NX + kx] = cplx<double>{xr[y], xi[y]};
+  }
+  __syncthreads();
+  cplx<double>* o = out + (size_t)d * NW;
+  for (int line = tid; line < P * NX; line += blockDim.x) {
+    const int ky = line / NX, kx = line % NX;
+    double xr[N], xi[N];
+#pragma unroll
+    for (int z = 0; z < N; ++z) { const cplx<double> v = buf[(z * P + ky) * NX + kx]; xr[z] = v.re; xi[z] = v.im; }
+    fft_fwd_pruned<P>(xr, xi, [&](int k, double re, double im) { o[(k * P + ky) * NX + kx] = cplx<double>{re, im}; });
+  }
+}
+
+template <typename R>
+__global__ void kernel_combine(const cplx<double>* __restrict__ lo, const cplx<double>* __restrict__ hi, int N,
+                               cplx<R>* __restrict__ kspec) {
+  const int P = 2 * N, NX = N + 1, NW = P * P * NX;
+  constexpr int T = ChunkT<R>::value;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)NW * kNOff) return;
+  const int d = (int)(idx / NW), w = (int)(idx % NW);
+  const int k0 = w / (P * NX);
+  const cplx<double> a = lo[idx], b = hi[idx];
+  const double sg = (k0 & 1) ? -1.0 : 1.0;
+  // layout [chunk][343][T]
+  kspec[((size_t)(w / T) * kNOff + d) * T + (w % T)] = cplx<R>{(R)(a.re + sg * b.re), (R)(a.im + sg * b.im)};
+}
+
+template <typename Kern>
+static cudaError_t set_smem(Kern k, size_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R>
+cudaError_t launch_fft_forward(int N, const R* nodes, const int* gids, const int* sids, int count, void* spec,
+                               int spec_blocks, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  cplx<R>* sp = reinterpret_cast<cplx<R>*>(spec);
+  if (N == 16) {
+    const size_t sm = sizeof(cplx<R>) * 16 * 32 * 17;
+    cudaError_t e = set_smem(fft_fwd_kernel<R, 16>, sm);
+    if (e != cudaSuccess) return e;
+    fft_fwd_kernel<R, 16><<<count, 256, sm, s>>>(nodes, gids, sids, sp, spec_blocks);
+  } else if (N == 8) {
+    const size_t sm = sizeof(cplx<R>) * 8 * 16 * 9;
+    fft_fwd_kernel<R, 8><<<count, 64, sm, s>>>(nodes, gids, sids, sp, spec_blocks);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_fft_inverse(int N, const void* acc, int spec_blocks, const int* sids, const int* gids,
+                               const double* scales, int count, R* out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const cplx<R>* ac = reinterpret_cast<const cplx<R>*>(acc);
+  if (N == 16) {
+    const size_t sm = sizeof(cplx<R>) * 16 * 32 * 17;
+    cudaError_t e = set_smem(fft_inv_kernel<R, 16>, sm);
+    if (e != cudaSuccess) return e;
+    fft_inv_kernel<R, 16><<<count, 256, sm, s>>>(ac, spec_blocks, sids, gids, scales, out);
+  } else if (N == 8) {
+    const size_t sm = sizeof(cplx<R>) * 8 * 16 * 9;
+    fft_inv_kernel<R, 8><<<count, 64, sm, s>>>(ac, spec_blocks, sids, gids, scales, out);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_kernel_spectra(int N, const double* karr, void* kspec_level, double* tmp, cudaStream_t s) {
+  const int P = 2 * N, NW = P * P * (N + 1);
+  cplx<double>* lo = reinterpret_cast<cplx<double>*>(tmp);
+  cplx<double>* hi = lo + (size_t)kNOff * NW;
+  const size_t sm = sizeof(cplx<double>) * N * P * (N + 1);
+  cudaError_t e;
+  if (N == 16) {
+    if ((e = set_smem(fft_kernel_half<16>, sm)) != cudaSuccess) return e;
+    fft_kernel_half<16><<<kNOff, 256, sm, s>>>(karr, 0, lo);
+    fft_kernel_half<16><<<kNOff, 256, sm, s>>>(karr, 16, hi);
+  } else if (N == 8) {
+    fft_kernel_half<8><<<kNOff, 64, sm, s>>>(karr, 0, lo);
+    fft_kernel_half<8><<<kNOff, 64, sm, s>>>(karr, 8, hi);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t total = (size_t)NW * kNOff;
+  kernel_combine<R><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(lo, hi, N, reinterpret_cast<cplx<R>*>(kspec_level));
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fft_forward<float>(int, const float*, const int*, const int*, int, void*, int, cudaStream_t);
+template cudaError_t launch_fft_forward<double>(int, const double*, const int*, const int*, int, void*, int, cudaStream_t);
+template cudaError_t launch_fft_inverse<float>(int, const void*, int, const int*, const int*, const double*, int, float*, cudaStream_t);
+template cudaError_t launch_fft_inverse<double>(int, const void*, int, const int*, const int*, const double*, int, double*, cudaStream_t);
+template cudaError_t launch_kernel_spectra<float>(int, const double*, void*, double*, cudaStream_t);
+template cudaError_t launch_kernel_spectra<double>(int, const double*, void*, double*, cudaStream_t);
+
+}  // namespace flgf

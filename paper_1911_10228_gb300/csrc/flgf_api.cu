@@ -1,0 +1,1012 @@
+// Host side of the FLGF library: context set-up (LGF table, kernel spectra),
+// block-set compilation (mesh checks, octrees, interaction tiles, launch
+// lists) and the solve sequence of Sec. 2.1 / Sec. 3.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/flgf.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace flgf;
+
+struct flgf_ctx {
+  int N = 16, nI = 6, prec = FLGF_FP64, max_oct = 6, R = 100, RA = 600;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double* d_table = nullptr;
+  double* d_J1 = nullptr;
+  void* d_kspec = nullptr;
+  size_t kstride = 0;  // complex elements per octree level
+  std::vector<double> J1;
+};
+
+namespace {
+
+using I3 = std::array<int, 3>;
+
+int fail(flgf_ctx* c, int code, const std::string& m) {
+  if (c) c->err = m;
+  return code;
+}
+
+#define CK(call)                                                                                     \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return fail(ctx, FLGF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+inline uint64_t key3(int a, int b, int c) {
+  const uint64_t o = 1u << 20;
+  return ((uint64_t)(a + o) << 42) | ((uint64_t)(b + o) << 21) | (uint64_t)(c + o);
+}
+inline uint64_t key3(const I3& v) { return key3(v[0], v[1], v[2]); }
+
+// 1-D Lagrange interpolation from the N parent nodes (positions 0, 2, ..,
+// 2N-2) to the 2N nodes of the two children (positions 0..2N-1): even rows
+// copy the coinciding node; odd rows interpolate on n_I consecutive nodes
+// centred on the point and shifted inwards at the faces (Sec. 2.1).
+std::vector<double> lagrange_matrix(int N, int nI) {
+  std::vector<double> J((size_t)2 * N * N, 0.0);
+  for (int j = 0; j < 2 * N; ++j) {
+    if (j % 2 == 0) {
+      J[(size_t)j * N + j / 2] = 1.0;
+      continue;
+    }
+    int start = (j + 1) / 2 - nI / 2;
+    start = std::min(std::max(start, 0), N - nI);
+    for (int m = 0; m < nI; ++m) {
+      const double xm = 2.0 * (start + m);
+      double w = 1.0;
+      for (int q = 0; q < nI; ++q)
+        if (q != m) {
+          const double xq = 2.0 * (start + q);
+          w *= ((double)j - xq) / (xm - xq);
+        }
+      J[(size_t)j * N + start + m] = w;
+    }
+  }
+  return J;
+}
+
+// Bump allocator that collects host arrays and uploads them in one copy.
+struct Arena {
+  std::vector<char> host;
+  char* dev = nullptr;
+  template <typename T>
+  size_t add(const T* p, size_t n) {
+    size_t off = (host.size() + 255) & ~(size_t)255;
+    host.resize(off + n * sizeof(T));
+    if (n) std::memcpy(host.data() + off, p, n * sizeof(T));
+    return off;
+  }
+  template <typename T>
+  size_t add(const std::vector<T>& v) { return add(v.data(), v.size()); }
+  template <typename T>
+  T* at(size_t off) const { return reinterpret_cast<T*>(dev + off); }
+};
+
+struct Inst {  // one FMM over one refinement level of one problem
+  int p, l, variant;
+  int top = 0;
+  std::vector<std::vector<I3>> lv;                       // block coords per octree level
+  std::vector<std::unordered_map<uint64_t, int>> idx;    // coords -> index per level
+  std::vector<int> gid0;                                 // first global id per level
+  std::vector<std::vector<uint8_t>> is_src, need_tgt;
+  double h = 1.0;
+};
+
+struct LevelInfo {
+  std::vector<I3> c;
+  std::vector<uint8_t> leaf;
+  std::unordered_map<uint64_t, int> idx;
+  int fw0 = 0;      // first block in fuser / fwork
+  int ugid0 = 0;    // first global id of u^l (instance 0, octree level 0)
+  int inst0 = -1, inst1 = -1;
+  double h = 1.0;
+  size_t nbr6_off = 0;  // arena offset of the face-neighbour table
+};
+
+struct Problem {
+  int L = 1;
+  double h0 = 1.0;
+  std::vector<LevelInfo> lev;
+};
+
+struct PhaseOff {  // arena offsets and counts of one phase's launch lists
+  int gid_begin = 0, nblocks = 0;
+  int n_prep = 0; size_t prep_src = 0, prep_dst = 0, prep_zero = 0;
+  std::vector<int> n_ant; std::vector<size_t> ant_par, ant_ch;
+  int n_fwd = 0; size_t fwd_gid = 0, fwd_sid = 0;
+  int n_tiles = 0, max_par = 0, max_cells = 0; size_t tiles = 0, src_ids = 0, tgt_ids = 0;
+  int n_inv = 0; size_t inv_sid = 0, inv_gid = 0, inv_scale = 0;
+  std::vector<int> n_itp; std::vector<size_t> itp_ch, itp_par, itp_cpos;
+  int n_sel = 0; size_t sel_src = 0, sel_dst = 0;
+  int n_acc = 0; size_t acc_nbr = 0, acc_fine = 0, acc_cpos = 0;
+  int n_cor = 0; size_t cor_nbr = 0, cor_fine = 0, cor_cpos = 0, cor_ih2 = 0;
+  int n_crs = 0; size_t crs_coarse = 0, crs_fine = 0;  // coarsening of level l from l+1
+};
+
+}  // namespace
+
+struct flgf_blockset {
+  flgf_ctx* ctx = nullptr;
+  std::vector<Problem> prob;
+  std::vector<Inst> inst;
+  std::vector<PhaseOff> ph;
+  int Lmax = 0, G = 0, B = 0, max_phase_blocks = 0, max_level_blocks = 0;
+  int64_t dof = 0, pairs = 0, n_fwd = 0, n_inv = 0, n_koff = 0;
+  Arena ar;
+  void* nodes = nullptr;
+  void* unodes = nullptr;
+  void* fuser = nullptr;
+  void* fwork = nullptr;
+  void* spec = nullptr;
+  void* acc = nullptr;
+  void* lap_in = nullptr;
+  void* lap_out = nullptr;
+  int* d_err = nullptr;
+  bool correction = true, solved = false;
+  bool use_graph = false, timing = false;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;  // (stage, (start, end))
+  size_t ev_used = 0;
+  double stage_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+  int timed_solves = 0;
+  bool ev_pending = false;
+};
+
+// ----------------------------------------------------------------------------
+// Context
+// ----------------------------------------------------------------------------
+extern "C" void flgf_default_opts(flgf_opts* o) {
+  if (!o) return;
+  o->N = 16;
+  o->n_interp = 6;
+  o->precision = FLGF_FP64;
+  o->max_oct_levels = 6;
+  o->table_radius = 100;
+  o->asym_radius = 600;
+  o->stream = nullptr;
+}
+
+extern "C" const char* flgf_last_error(const flgf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" void flgf_destroy(flgf_ctx* ctx) {
+  if (!ctx) return;
+  cudaFree(ctx->d_table);
+  cudaFree(ctx->d_J1);
+  cudaFree(ctx->d_kspec);
+  delete ctx;
+}
+
+extern "C" int flgf_create(flgf_ctx** out, const flgf_opts* o) {
+  if (!out || !o) return FLGF_EINVAL;
+  *out = nullptr;
+  flgf_ctx* ctx = new (std::nothrow) flgf_ctx();
+  if (!ctx) return FLGF_ENOMEM;
+  auto bad = [&](const std::string& m) { delete ctx; (void)m; return FLGF_EINVAL; };
+  if (o->N != 8 && o->N != 16) return bad("N must be 8 or 16");
+  if (o->n_interp < 2 || o->n_interp > std::min(o->N, 10)) return bad("n_interp out of range");
+  if (o->precision != FLGF_FP64 && o->precision != FLGF_FP32) return bad("precision");
+  if (o->max_oct_levels < 1 || o->max_oct_levels > 8) return bad("max_oct_levels");
+  if (o->table_radius < 1 || o->table_radius > 200 || o->asym_radius < o->table_radius) return bad("radii");
+  ctx->N = o->N;
+  ctx->nI = o->n_interp;
+  ctx->prec = o->precision;
+  ctx->max_oct = o->max_oct_levels;
+  ctx->R = o->table_radius;
+  ctx->RA = o->asym_radius;
+  ctx->stream = (cudaStream_t)o->stream;
+  ctx->J1 = lagrange_matrix(ctx->N, ctx->nI);
+  const int N = ctx->N, P = 2 * N, NW = nfreq(N);
+  const int R = ctx->R;
+  double* B = nullptr;
+  double* karr = nullptr;
+  double* tmp = nullptr;
+  auto cleanup = [&]() { cudaFree(B); cudaFree(karr); cudaFree(tmp); };
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return FLGF_OK;
+    ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return FLGF_ECUDA;
+  };
+  int rc;
+#define STEP(call)                          \
+  if ((rc = ck((call), #call)) != FLGF_OK) { \
+    cleanup();                              \
+    flgf_destroy(ctx);                      \
+    return rc;                              \
+  }
+  STEP(fft_init_constants());
+  STEP(cudaMalloc(&ctx->d_J1, sizeof(double) * ctx->J1.size()));
+  STEP(cudaMemcpy(ctx->d_J1, ctx->J1.data(), sizeof(double) * ctx->J1.size(), cudaMemcpyHostToDevice));
+  const size_t nq = (size_t)quad_nodes();
+  STEP(cudaMalloc(&B, sizeof(double) * (R + 2) * nq));
+  STEP(cudaMalloc(&ctx->d_table, sizeof(double) * (size_t)(R + 1) * (R + 1) * (R + 1)));
+  STEP(cudaMemsetAsync(ctx->d_table, 0, sizeof(double) * (size_t)(R + 1) * (R + 1) * (R + 1), ctx->stream));
+  STEP(launch_bessel_table(B, R, ctx->stream));
+  STEP(launch_lgf_table(B, R, ctx->d_table, R, ctx->stream));
+  const size_t csz = ctx->prec == FLGF_FP64 ? 16 : 8;
+  ctx->kstride = (size_t)kNOff * NW;
+  STEP(cudaMalloc(&ctx->d_kspec, csz * ctx->kstride * ctx->max_oct));
+  STEP(cudaMalloc(&karr, sizeof(double) * (size_t)kNOff * P * P * P));
+  STEP(cudaMalloc(&tmp, 2 * 16 * (size_t)kNOff * NW));
+  for (int k = 0; k < ctx->max_oct; ++k) {
+    STEP(launch_kernel_arrays(ctx->d_table, R, (double)R, (double)ctx->RA, N, k, karr, ctx->stream));
+    void* lvl = (char*)ctx->d_kspec + csz * ctx->kstride * k;
+    if (ctx->prec == FLGF_FP64) {
+      STEP(launch_kernel_spectra<double>(N, karr, lvl, tmp, ctx->stream));
+    } else {
+      STEP(launch_kernel_spectra<float>(N, karr, lvl, tmp, ctx->stream));
+    }
+  }
+  STEP(cudaStreamSynchronize(ctx->stream));
+#undef STEP
+  cleanup();
+  *out = ctx;
+  return FLGF_OK;
+}
+
+extern "C" int flgf_lgf_eval(flgf_ctx* ctx, int n, const int32_t* pts, double* out) {
+  if (!ctx || n < 0 || (n > 0 && (!pts || !out))) return fail(ctx, FLGF_EINVAL, "lgf_eval: bad arguments");
+  if (n == 0) return FLGF_OK;
+  int32_t* dp = nullptr;
+  double* dv = nullptr;
+  CK(cudaMalloc(&dp, sizeof(int32_t) * 3 * n));
+  cudaError_t e = cudaMalloc(&dv, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dp, pts, sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = launch_lgf_eval(ctx->d_table, ctx->R, (double)ctx->R, (double)ctx->RA, dp, n, dv, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dv, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(dp);
+  cudaFree(dv);
+  if (e != cudaSuccess) return fail(ctx, FLGF_ECUDA, std::string("lgf_eval: ") + cudaGetErrorString(e));
+  return FLGF_OK;
+}
+
+extern "C" int flgf_kernel_spectrum(flgf_ctx* ctx, int k, int d0, int d1, int d2, double* out) {
+  if (!ctx || !out || k < 0 || k >= ctx->max_oct || std::abs(d0) > 3 || std::abs(d1) > 3 || std::abs(d2) > 3)
+    return fail(ctx, FLGF_EINVAL, "kernel_spectrum: bad arguments");
+  const int N = ctx->N, NW = nfreq(N);
+  const int d = off_index(d0, d1, d2);
+  const bool f64 = ctx->prec == FLGF_FP64;
+  const int T = f64 ? 2 : 4;
+  const size_t csz = f64 ? 16 : 8;
+  std::vector<char> lvl(csz * ctx->kstride);
+  CK(cudaMemcpyAsync(lvl.data(), (char*)ctx->d_kspec + csz * ctx->kstride * k, lvl.size(), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int w = 0; w < NW; ++w) {
+    const size_t ix = ((size_t)(w / T) * kNOff + d) * T + (w % T);
+    if (f64) {
+      const double* v = reinterpret_cast<const double*>(lvl.data()) + 2 * ix;
+      out[2 * w] = v[0];
+      out[2 * w + 1] = v[1];
+    } else {
+      const float* v = reinterpret_cast<const float*>(lvl.data()) + 2 * ix;
+      out[2 * w] = v[0];
+      out[2 * w + 1] = v[1];
+    }
+  }
+  return FLGF_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Block set compilation
+// ----------------------------------------------------------------------------
+namespace {
+
+int build_octree(Inst& in, const std::vector<I3>& base, int max_oct, std::string& err) {
+  in.lv.clear();
+  in.lv.push_back(base);
+  int k = 0;
+  while (true) {
+    I3 lo = {INT32_MAX, INT32_MAX, INT32_MAX}, hi = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (const auto& c : in.lv[k])
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], c[a] >> 1);
+        hi[a] = std::max(hi[a], c[a] >> 1);
+      }
+    if (hi[0] - lo[0] <= 1 && hi[1] - lo[1] <= 1 && hi[2] - lo[2] <= 1) break;
+    std::vector<I3> par;
+    par.reserve(in.lv[k].size());
+    for (const auto& c : in.lv[k]) par.push_back({c[0] >> 1, c[1] >> 1, c[2] >> 1});
+    std::sort(par.begin(), par.end());
+    par.erase(std::unique(par.begin(), par.end()), par.end());
+    in.lv.push_back(par);
+    ++k;
+  }
+  in.top = k;
+  if (in.top + 1 > max_oct) {
+    err = "block set needs " + std::to_string(in.top + 1) + " octree levels; context caches " +
+          std::to_string(max_oct) + " (raise max_oct_levels)";
+    return FLGF_EINVAL;
+  }
+  in.idx.assign(in.lv.size(), {});
+  for (size_t q = 0; q < in.lv.size(); ++q)
+    for (size_t i = 0; i < in.lv[q].size(); ++i) in.idx[q][key3(in.lv[q][i])] = (int)i;
+  return FLGF_OK;
+}
+
+}  // namespace
+
+extern "C" void flgf_blockset_destroy(flgf_blockset* bs) {
+  if (!bs) return;
+  if (bs->gexec) cudaGraphExecDestroy(bs->gexec);
+  for (auto& e : bs->ev) {
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  cudaFree(bs->ar.dev);
+  cudaFree(bs->nodes);
+  cudaFree(bs->unodes);
+  cudaFree(bs->fuser);
+  cudaFree(bs->fwork);
+  cudaFree(bs->spec);
+  cudaFree(bs->acc);
+  cudaFree(bs->lap_in);
+  cudaFree(bs->lap_out);
+  cudaFree(bs->d_err);
+  delete bs;
+}
+
+extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
+                                    const int32_t* coords, const double* h0, flgf_blockset** out) {
+  if (!ctx || !out || n_problems < 1 || !n_levels || !nblk || !coords || !h0)
+    return fail(ctx, FLGF_EINVAL, "blockset_create: bad arguments");
+  *out = nullptr;
+  const int N = ctx->N;
+  const size_t N3 = (size_t)N * N * N;
+  auto bs = new (std::nothrow) flgf_blockset();
+  if (!bs) return fail(ctx, FLGF_ENOMEM, "host allocation");
+  bs->ctx = ctx;
+  auto bail = [&](int code, const std::string& m) {
+    flgf_blockset_destroy(bs);
+    return fail(ctx, code, m);
+  };
+  // ---- read and validate the mesh ------------------------------------------
+  int q = 0;
+  size_t ci = 0;
+  bs->prob.resize(n_problems);
+  for (int p = 0; p < n_problems; ++p) {
+    Problem& P = bs->prob[p];
+    P.L = n_levels[p];
+    P.h0 = h0[p];
+    if (P.L < 1 || P.L > 16) return bail(FLGF_EINVAL, "n_levels out of range");
+    if (!(P.h0 > 0.0)) return bail(FLGF_EINVAL, "h0 must be positive");
+    P.lev.resize(P.L);
+    for (int l = 0; l < P.L; ++l, ++q) {
+      LevelInfo& L = P.lev[l];
+      const int nb = nblk[q];
+      if (nb < 1) return bail(FLGF_EINVAL, "every level needs at least one block");
+      L.c.resize(nb);
+      for (int b = 0; b < nb; ++b, ++ci) {
+        for (int a = 0; a < 3; ++a) {
+          const int v = coords[3 * ci + a];
+          if (v < -(1 << 19) || v >= (1 << 19)) return bail(FLGF_EINVAL, "block coordinate out of range");
+          L.c[b][a] = v;
+        }
+        if (!L.idx.emplace(key3(L.c[b]), b).second)
+          return bail(FLGF_EMESH, "duplicate block in problem " + std::to_string(p) + " level " + std::to_string(l));
+      }
+      L.h = P.h0 / (double)(1 << l);
+      bs->max_level_blocks = std::max(bs->max_level_blocks, nb);
+    }
+    for (int l = 0; l < P.L; ++l) {
+      LevelInfo& L = P.lev[l];
+      L.leaf.assign(L.c.size(), 1);
+      if (l + 1 < P.L) {
+        const LevelInfo& F = P.lev[l + 1];
+        std::vector<int> nkids(L.c.size(), 0);
+        for (const auto& c : F.c) {
+          auto it = L.idx.find(key3(c[0] >> 1, c[1] >> 1, c[2] >> 1));
+          if (it == L.idx.end())
+            return bail(FLGF_EMESH, "level " + std::to_string(l + 1) + " block without a parent (problem " +
+                                        std::to_string(p) + ")");
+          nkids[it->second]++;
+        }
+        for (size_t b = 0; b < L.c.size(); ++b) {
+          if (nkids[b] != 0 && nkids[b] != 8)
+            return bail(FLGF_EMESH, "partially refined block (problem " + std::to_string(p) + ", level " +
+                                        std::to_string(l) + ")");
+          L.leaf[b] = nkids[b] == 0;
+        }
+        for (size_t b = 0; b < L.c.size(); ++b) {
+          if (L.leaf[b]) continue;
+          for (int e = 0; e < 27; ++e) {
+            if (e == 13) continue;
+            const I3 nbc = {L.c[b][0] + e / 9 - 1, L.c[b][1] + (e / 3) % 3 - 1, L.c[b][2] + e % 3 - 1};
+            if (!L.idx.count(key3(nbc)))
+              return bail(FLGF_EMESH, "refined block lacks its 26-neighbour buffer (problem " + std::to_string(p) +
+                                          ", level " + std::to_string(l) + ")");
+          }
+        }
+      }
+      for (size_t b = 0; b < L.c.size(); ++b) bs->dof += L.leaf[b] ? (int64_t)N3 : 0;
+    }
+    bs->Lmax = std::max(bs->Lmax, P.L);
+  }
+  // ---- level storage -------------------------------------------------------
+  for (auto& P : bs->prob)
+    for (auto& L : P.lev) {
+      L.fw0 = bs->B;
+      bs->B += (int)L.c.size();
+    }
+  // ---- instances and global ids, phase by phase ----------------------------
+  bs->ph.resize(bs->Lmax);
+  std::string err;
+  for (int l = 0; l < bs->Lmax; ++l) {
+    PhaseOff& ph = bs->ph[l];
+    ph.gid_begin = bs->G;
+    for (int p = 0; p < n_problems; ++p) {
+      Problem& P = bs->prob[p];
+      if (l >= P.L) continue;
+      LevelInfo& L = P.lev[l];
+      const bool has_nonleaf = std::any_of(L.leaf.begin(), L.leaf.end(), [](uint8_t v) { return v == 0; });
+      for (int variant = 0; variant < (has_nonleaf ? 2 : 1); ++variant) {
+        Inst in;
+        in.p = p;
+        in.l = l;
+        in.variant = variant;
+        in.h = L.h;
+        int rc = build_octree(in, L.c, ctx->max_oct, err);
+        if (rc != FLGF_OK) return bail(rc, err);
+        in.gid0.resize(in.lv.size());
+        in.is_src.resize(in.lv.size());
+        in.need_tgt.resize(in.lv.size());
+        for (size_t k = 0; k < in.lv.size(); ++k) {
+          in.gid0[k] = bs->G;
+          bs->G += (int)in.lv[k].size();
+          in.is_src[k].assign(in.lv[k].size(), 1);
+          in.need_tgt[k].assign(in.lv[k].size(), variant == 0 ? 1 : 0);
+        }
+        if (variant == 1) {
+          for (size_t b = 0; b < L.c.size(); ++b) {
+            in.is_src[0][b] = L.leaf[b];
+            if (!L.leaf[b]) {  // target: this block and its ancestors
+              I3 c = L.c[b];
+              for (size_t k = 0; k < in.lv.size(); ++k) {
+                in.need_tgt[k][in.idx[k][key3(c)]] = 1;
+                c = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
+              }
+            }
+          }
+          L.inst1 = (int)bs->inst.size();
+        } else {
+          L.inst0 = (int)bs->inst.size();
+          L.ugid0 = in.gid0[0];
+        }
+        bs->inst.push_back(std::move(in));
+      }
+    }
+    ph.nblocks = bs->G - ph.gid_begin;
+    bs->max_phase_blocks = std::max(bs->max_phase_blocks, ph.nblocks);
+  }
+  // ---- launch lists ----------------------------------------------------------
+  Arena& ar = bs->ar;
+  const int TP[3] = {4, 8, 8};  // tile size in parents
+  for (int l = 0; l < bs->Lmax; ++l) {
+    PhaseOff& ph = bs->ph[l];
+    std::vector<int> prep_src, prep_dst;
+    std::vector<uint8_t> prep_zero;
+    int maxtop = 0;
+    for (const auto& in : bs->inst)
+      if (in.l == l) maxtop = std::max(maxtop, in.top);
+    std::vector<std::vector<int>> ant_par(maxtop + 1), ant_ch(maxtop + 1);
+    std::vector<std::vector<int>> itp_ch(maxtop + 1), itp_par(maxtop + 1), itp_cpos(maxtop + 1);
+    std::vector<int> fwd_gid, fwd_sid, inv_sid, inv_gid;
+    std::vector<double> inv_scale;
+    std::vector<HadTile> tiles;
+    std::vector<int> src_ids, tgt_ids;
+    for (const auto& in : bs->inst) {
+      if (in.l != l) continue;
+      const LevelInfo& L = bs->prob[in.p].lev[l];
+      for (size_t b = 0; b < L.c.size(); ++b) {
+        prep_src.push_back(L.fw0 + (int)b);
+        prep_dst.push_back(in.gid0[0] + (int)b);
+        prep_zero.push_back(in.variant == 1 && !L.leaf[b]);
+      }
+      for (int k = 1; k <= in.top; ++k) {
+        for (size_t i = 0; i < in.lv[k].size(); ++i) {
+          const I3& c = in.lv[k][i];
+          ant_par[k].push_back(in.gid0[k] + (int)i);
+          for (int a = 0; a < 8; ++a) {
+            const I3 ch = {2 * c[0] + (a >> 2), 2 * c[1] + ((a >> 1) & 1), 2 * c[2] + (a & 1)};
+            auto it = in.idx[k - 1].find(key3(ch));
+            ant_ch[k].push_back(it == in.idx[k - 1].end() ? -1 : in.gid0[k - 1] + it->second);
+          }
+        }
+      }
+      for (size_t k = 0; k < in.lv.size(); ++k) {
+        for (size_t i = 0; i < in.lv[k].size(); ++i) {
+          const int gid = in.gid0[k] + (int)i;
+          if (in.is_src[k][i]) {
+            fwd_gid.push_back(gid);
+            fwd_sid.push_back(gid - ph.gid_begin);
+          }
+          if (in.need_tgt[k][i]) {
+            inv_sid.push_back(gid - ph.gid_begin);
+            inv_gid.push_back(gid);
+            inv_scale.push_back(in.h * in.h);
+            if ((int)k < in.top) {
+              const I3& c = in.lv[k][i];
+              const int pi = in.idx[k + 1].at(key3(c[0] >> 1, c[1] >> 1, c[2] >> 1));
+              itp_ch[k].push_back(gid);
+              itp_par[k].push_back(in.gid0[k + 1] + pi);
+              itp_cpos[k].push_back(((c[0] & 1) << 2) | ((c[1] & 1) << 1) | (c[2] & 1));
+            }
+          }
+        }
+        // interaction tiles of this octree level
+        I3 lo = {INT32_MAX, INT32_MAX, INT32_MAX}, hi = {INT32_MIN, INT32_MIN, INT32_MIN};
+        for (const auto& c : in.lv[k])
+          for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], c[a] >> 1);
+            hi[a] = std::max(hi[a], c[a] >> 1);
+          }
+        auto lookup = [&](int a, int b, int c2) -> int {
+          auto it = in.idx[k].find(key3(a, b, c2));
+          return it == in.idx[k].end() ? -1 : it->second;
+        };
+        const bool excl = k > 0;
+        for (int t0 = lo[0]; t0 <= hi[0]; t0 += TP[0])
+          for (int t1 = lo[1]; t1 <= hi[1]; t1 += TP[1])
+            for (int t2 = lo[2]; t2 <= hi[2]; t2 += TP[2]) {
+              HadTile tl;
+              tl.level = (int)k;
+              tl.excl_near = excl ? 1 : 0;
+              const int t[3] = {t0, t1, t2};
+              for (int a = 0; a < 3; ++a) {
+                tl.p0[a] = t[a];
+                tl.P[a] = std::min(TP[a], hi[a] - t[a] + 1);
+                tl.r0[a] = std::max(t[a] - 1, lo[a]);
+                tl.Rg[a] = std::min(t[a] + tl.P[a], hi[a]) - tl.r0[a] + 1;
+              }
+              std::vector<int> tg;
+              bool any = false;
+              for (int x = 0; x < 2 * tl.P[0]; ++x)
+                for (int y = 0; y < 2 * tl.P[1]; ++y)
+                  for (int z = 0; z < 2 * tl.P[2]; ++z) {
+                    const int i = lookup(2 * t0 + x, 2 * t1 + y, 2 * t2 + z);
+                    const bool need = i >= 0 && in.need_tgt[k][i];
+                    tg.push_back(need ? in.gid0[k] + i - ph.gid_begin : -1);
+                    any |= need;
+                  }
+              if (!any) continue;
+              std::vector<int> sg;
+              for (int x = 0; x < 2 * tl.Rg[0]; ++x)
+                for (int y = 0; y < 2 * tl.Rg[1]; ++y)
+                  for (int z = 0; z < 2 * tl.Rg[2]; ++z) {
+                    const int i = lookup(2 * tl.r0[0] + x, 2 * tl.r0[1] + y, 2 * tl.r0[2] + z);
+                    sg.push_back(i >= 0 && in.is_src[k][i] ? in.gid0[k] + i - ph.gid_begin : -1);
+                  }
+              // count interacting (target, source) pairs for the work accounting
+              for (int x = 0; x < 2 * tl.P[0]; ++x)
+                for (int y = 0; y < 2 * tl.P[1]; ++y)
+                  for (int z = 0; z < 2 * tl.P[2]; ++z) {
+                    if (tg[(x * 2 * tl.P[1] + y) * 2 * tl.P[2] + z] < 0) continue;
+                    const int tc[3] = {2 * t0 + x, 2 * t1 + y, 2 * t2 + z};
+                    for (int sx = 0; sx < 2 * tl.Rg[0]; ++sx)
+                      for (int sy = 0; sy < 2 * tl.Rg[1]; ++sy)
+                        for (int sz = 0; sz < 2 * tl.Rg[2]; ++sz) {
+                          if (sg[(sx * 2 * tl.Rg[1] + sy) * 2 * tl.Rg[2] + sz] < 0) continue;
+                          const int sc[3] = {2 * tl.r0[0] + sx, 2 * tl.r0[1] + sy, 2 * tl.r0[2] + sz};
+                          bool inlist = true, near = true;
+                          for (int a = 0; a < 3; ++a) {
+                            if (std::abs((sc[a] >> 1) - (tc[a] >> 1)) > 1) inlist = false;
+                            if (std::abs(sc[a] - tc[a]) > 1) near = false;
+                          }
+                          if (inlist && !(excl && near)) bs->pairs++;
+                        }
+                  }
+              tl.tgt_off = (int)tgt_ids.size();
+              tgt_ids.insert(tgt_ids.end(), tg.begin(), tg.end());
+              tl.src_off = (int)src_ids.size();
+              src_ids.insert(src_ids.end(), sg.begin(), sg.end());
+              ph.max_par = std::max(ph.max_par, tl.P[0] * tl.P[1] * tl.P[2]);
+              ph.max_cells = std::max(ph.max_cells, 8 * tl.Rg[0] * tl.Rg[1] * tl.Rg[2]);
+              tiles.push_back(tl);
+            }
+      }
+    }
+    bs->n_fwd += (int64_t)fwd_gid.size();
+    bs->n_inv += (int64_t)inv_gid.size();
+    for (int k = 0; k <= maxtop; ++k) bs->n_koff += kNOff;
+    ph.n_prep = (int)prep_src.size();
+    ph.prep_src = ar.add(prep_src);
+    ph.prep_dst = ar.add(prep_dst);
+    ph.prep_zero = ar.add(prep_zero);
+    ph.n_ant.assign(maxtop + 1, 0);
+    ph.ant_par.assign(maxtop + 1, 0);
+    ph.ant_ch.assign(maxtop + 1, 0);
+    ph.n_itp.assign(maxtop + 1, 0);
+    ph.itp_ch.assign(maxtop + 1, 0);
+    ph.itp_par.assign(maxtop + 1, 0);
+    ph.itp_cpos.assign(maxtop + 1, 0);
+    for (int k = 0; k <= maxtop; ++k) {
+      ph.n_ant[k] = (int)ant_par[k].size();
+      ph.ant_par[k] = ar.add(ant_par[k]);
+      ph.ant_ch[k] = ar.add(ant_ch[k]);
+      ph.n_itp[k] = (int)itp_ch[k].size();
+      ph.itp_ch[k] = ar.add(itp_ch[k]);
+      ph.itp_par[k] = ar.add(itp_par[k]);
+      ph.itp_cpos[k] = ar.add(itp_cpos[k]);
+    }
+    ph.n_fwd = (int)fwd_gid.size();
+    ph.fwd_gid = ar.add(fwd_gid);
+    ph.fwd_sid = ar.add(fwd_sid);
+    ph.n_tiles = (int)tiles.size();
+    ph.tiles = ar.add(tiles);
+    ph.src_ids = ar.add(src_ids);
+    ph.tgt_ids = ar.add(tgt_ids);
+    ph.n_inv = (int)inv_gid.size();
+    ph.inv_sid = ar.add(inv_sid);
+    ph.inv_gid = ar.add(inv_gid);
+    ph.inv_scale = ar.add(inv_scale);
+    // multi-resolution coupling lists
+    std::vector<int> sel_src, sel_dst, acc_nbr, acc_fine, acc_cpos, cor_nbr, cor_fine, cor_cpos, crs_c, crs_f;
+    std::vector<double> cor_ih2;
+    for (int p = 0; p < n_problems; ++p) {
+      Problem& P = bs->prob[p];
+      if (l >= P.L) continue;
+      LevelInfo& L = P.lev[l];
+      if (L.inst1 >= 0) {
+        const Inst& i1 = bs->inst[L.inst1];
+        for (size_t b = 0; b < L.c.size(); ++b)
+          if (!L.leaf[b]) {
+            sel_src.push_back(i1.gid0[0] + (int)b);
+            sel_dst.push_back(L.ugid0 + (int)b);
+          }
+      }
+      auto nbr27 = [&](const LevelInfo& C, const I3& parent, std::vector<int>& outv) {
+        for (int e = 0; e < 27; ++e) {
+          auto it = C.idx.find(key3(parent[0] + e / 9 - 1, parent[1] + (e / 3) % 3 - 1, parent[2] + e % 3 - 1));
+          outv.push_back(it == C.idx.end() ? -1 : C.ugid0 + it->second);
+        }
+      };
+      if (l > 0) {
+        const LevelInfo& C = P.lev[l - 1];
+        for (size_t b = 0; b < L.c.size(); ++b) {
+          const I3& c = L.c[b];
+          nbr27(C, {c[0] >> 1, c[1] >> 1, c[2] >> 1}, acc_nbr);
+          acc_fine.push_back(L.ugid0 + (int)b);
+          acc_cpos.push_back(((c[0] & 1) << 2) | ((c[1] & 1) << 1) | (c[2] & 1));
+        }
+      }
+      if (l + 1 < P.L) {
+        const LevelInfo& F = P.lev[l + 1];
+        for (size_t b = 0; b < F.c.size(); ++b) {
+          const I3& c = F.c[b];
+          nbr27(L, {c[0] >> 1, c[1] >> 1, c[2] >> 1}, cor_nbr);
+          cor_fine.push_back(F.fw0 + (int)b);
+          cor_cpos.push_back(((c[0] & 1) << 2) | ((c[1] & 1) << 1) | (c[2] & 1));
+          cor_ih2.push_back(1.0 / (F.h * F.h));
+        }
+        for (size_t b = 0; b < L.c.size(); ++b) {
+          if (L.leaf[b]) continue;
+          crs_c.push_back(L.fw0 + (int)b);
+          const I3& c = L.c[b];
+          for (int a = 0; a < 8; ++a)
+            crs_f.push_back(F.fw0 + F.idx.at(key3(2 * c[0] + (a >> 2), 2 * c[1] + ((a >> 1) & 1), 2 * c[2] + (a & 1))));
+        }
+      }
+    }
+    ph.n_sel = (int)sel_src.size();
+    ph.sel_src = ar.add(sel_src);
+    ph.sel_dst = ar.add(sel_dst);
+    ph.n_acc = (int)acc_fine.size();
+    ph.acc_nbr = ar.add(acc_nbr);
+    ph.acc_fine = ar.add(acc_fine);
+    ph.acc_cpos = ar.add(acc_cpos);
+    ph.n_cor = (int)cor_fine.size();
+    ph.cor_nbr = ar.add(cor_nbr);
+    ph.cor_fine = ar.add(cor_fine);
+    ph.cor_cpos = ar.add(cor_cpos);
+    ph.cor_ih2 = ar.add(cor_ih2);
+    ph.n_crs = (int)crs_c.size();
+    ph.crs_coarse = ar.add(crs_c);
+    ph.crs_fine = ar.add(crs_f);
+  }
+  // face neighbours for the Laplacian
+  for (auto& P : bs->prob)
+    for (auto& L : P.lev) {
+      std::vector<int> n6;
+      for (const auto& c : L.c)
+        for (int a = 0; a < 3; ++a)
+          for (int sg = 0; sg < 2; ++sg) {
+            I3 y = c;
+            y[a] += sg == 0 ? 1 : -1;
+            auto it = L.idx.find(key3(y));
+            n6.push_back(it == L.idx.end() ? -1 : it->second);
+          }
+      L.nbr6_off = ar.add(n6);
+    }
+  // ---- device memory ---------------------------------------------------------
+  const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4;
+  const size_t NW = (size_t)nfreq(N);
+  auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 256)); };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = alloc((void**)&ar.dev, ar.host.size());
+  if (e == cudaSuccess) e = cudaMemcpy(ar.dev, ar.host.data(), ar.host.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = alloc(&bs->nodes, rs * N3 * bs->G);
+  if (e == cudaSuccess) e = alloc(&bs->unodes, rs * N3 * bs->G);
+  if (e == cudaSuccess) e = alloc(&bs->fuser, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = alloc(&bs->fwork, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = alloc(&bs->spec, 2 * rs * NW * bs->max_phase_blocks);
+  if (e == cudaSuccess) e = alloc(&bs->acc, 2 * rs * NW * bs->max_phase_blocks);
+  if (e == cudaSuccess) e = alloc(&bs->lap_in, rs * N3 * bs->max_level_blocks);
+  if (e == cudaSuccess) e = alloc(&bs->lap_out, rs * N3 * bs->max_level_blocks);
+  if (e == cudaSuccess) e = alloc((void**)&bs->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(bs->fuser, 0, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = cudaMemset(bs->unodes, 0, rs * N3 * bs->G);
+  if (e == cudaSuccess) e = cudaMemset(bs->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? FLGF_ENOMEM : FLGF_ECUDA;
+    return bail(code, std::string("blockset allocation: ") + cudaGetErrorString(e));
+  }
+  *out = bs;
+  return FLGF_OK;
+}
+
+extern "C" int64_t flgf_blockset_dof(const flgf_blockset* bs) { return bs ? bs->dof : -1; }
+
+extern "C" int flgf_work_counts(const flgf_blockset* bs, int64_t* pairs, int64_t* fwd, int64_t* inv, int64_t* koff) {
+  if (!bs) return FLGF_EINVAL;
+  if (pairs) *pairs = bs->pairs;
+  if (fwd) *fwd = bs->n_fwd;
+  if (inv) *inv = bs->n_inv;
+  if (koff) *koff = bs->n_koff;
+  return FLGF_OK;
+}
+
+namespace {
+
+int check_pl(flgf_blockset* bs, int problem, int level) {
+  if (problem < 0 || problem >= (int)bs->prob.size()) return FLGF_EINVAL;
+  if (level < 0 || level >= bs->prob[problem].L) return FLGF_EINVAL;
+  return FLGF_OK;
+}
+
+cudaMemcpyKind kind(int where, bool to_dev) {
+  if (where == FLGF_DEVICE) return cudaMemcpyDeviceToDevice;
+  return to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+}
+
+}  // namespace
+
+extern "C" int flgf_load_source(flgf_blockset* bs, int problem, int level, const void* f, int where) {
+  if (!bs || !f || (where != FLGF_HOST && where != FLGF_DEVICE)) return FLGF_EINVAL;
+  flgf_ctx* ctx = bs->ctx;
+  if (check_pl(bs, problem, level) != FLGF_OK) return fail(ctx, FLGF_EINVAL, "load_source: bad problem/level");
+  const LevelInfo& L = bs->prob[problem].lev[level];
+  const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4, N3 = (size_t)ctx->N * ctx->N * ctx->N;
+  CK(cudaMemcpyAsync((char*)bs->fuser + rs * N3 * L.fw0, f, rs * N3 * L.c.size(), kind(where, true), ctx->stream));
+  if (where == FLGF_HOST) CK(cudaStreamSynchronize(ctx->stream));
+  return FLGF_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Solve
+// ----------------------------------------------------------------------------
+namespace {
+
+struct StageScope {
+  flgf_blockset* bs;
+  int stage;
+  cudaEvent_t end = nullptr;
+  StageScope(flgf_blockset* b, int s) : bs(b), stage(s) {
+    if (!bs->timing) return;
+    if (bs->ev_used == bs->ev.size()) {
+      cudaEvent_t a, c;
+      cudaEventCreate(&a);
+      cudaEventCreate(&c);
+      bs->ev.push_back({s, {a, c}});
+    }
+    auto& slot = bs->ev[bs->ev_used++];
+    slot.first = s;
+    cudaEventRecord(slot.second.first, bs->ctx->stream);
+    end = slot.second.second;
+  }
+  ~StageScope() {
+    if (end) cudaEventRecord(end, bs->ctx->stream);
+  }
+};
+
+template <typename R>
+cudaError_t enqueue_solve(flgf_blockset* bs) {
+  flgf_ctx* c = bs->ctx;
+  const int N = c->N;
+  cudaStream_t s = c->stream;
+  const Arena& ar = bs->ar;
+  R* nodes = (R*)bs->nodes;
+  R* unodes = (R*)bs->unodes;
+  R* fwork = (R*)bs->fwork;
+  const size_t N3 = (size_t)N * N * N;
+  cudaError_t e;
+#define RUN(x)                              \
+  if ((e = (x)) != cudaSuccess) return e;
+  RUN(cudaMemcpyAsync(fwork, bs->fuser, sizeof(R) * N3 * bs->B, cudaMemcpyDeviceToDevice, s));
+  {
+    StageScope sc(bs, 0);
+    for (int l = bs->Lmax - 2; l >= 0; --l) {
+      const PhaseOff& ph = bs->ph[l];
+      RUN(launch_coarsen<R>(N, fwork, ar.at<int>(ph.crs_fine), fwork, ar.at<int>(ph.crs_coarse), ph.n_crs, s));
+    }
+  }
+  for (int l = 0; l < bs->Lmax; ++l) {
+    const PhaseOff& ph = bs->ph[l];
+    const int maxtop = (int)ph.n_ant.size() - 1;
+    {
+      StageScope sc(bs, 1);
+      RUN(launch_copy_blocks<R>(N, fwork, ar.at<int>(ph.prep_src), nodes, ar.at<int>(ph.prep_dst),
+                                ar.at<uint8_t>(ph.prep_zero), ph.n_prep, s));
+      for (int k = 1; k <= maxtop; ++k)
+        RUN(launch_anterp<R>(N, c->d_J1, ar.at<int>(ph.ant_par[k]), ar.at<int>(ph.ant_ch[k]), ph.n_ant[k], nodes, s));
+    }
+    {
+      StageScope sc(bs, 2);
+      RUN(launch_fft_forward<R>(N, nodes, ar.at<int>(ph.fwd_gid), ar.at<int>(ph.fwd_sid), ph.n_fwd, bs->spec,
+                                ph.nblocks, s));
+    }
+    {
+      StageScope sc(bs, 3);
+      RUN(launch_hadamard<R>(N, ar.at<HadTile>(ph.tiles), ph.n_tiles, ph.max_par, ph.max_cells, ar.at<int>(ph.src_ids),
+                             ar.at<int>(ph.tgt_ids), bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
+    }
+    {
+      StageScope sc(bs, 4);
+      RUN(launch_fft_inverse<R>(N, bs->acc, ph.nblocks, ar.at<int>(ph.inv_sid), ar.at<int>(ph.inv_gid),
+                                ar.at<double>(ph.inv_scale), ph.n_inv, unodes, s));
+    }
+    {
+      StageScope sc(bs, 5);
+      for (int k = maxtop - 1; k >= 0; --k)
+        RUN(launch_interp_add<R>(N, c->d_J1, ar.at<int>(ph.itp_ch[k]), ar.at<int>(ph.itp_par[k]),
+                                 ar.at<int>(ph.itp_cpos[k]), ph.n_itp[k], unodes, s));
+    }
+    {
+      StageScope sc(bs, 6);
+      RUN(launch_copy_blocks<R>(N, unodes, ar.at<int>(ph.sel_src), unodes, ar.at<int>(ph.sel_dst), nullptr, ph.n_sel, s));
+      RUN(launch_cf_interp<R>(N, unodes, ar.at<int>(ph.acc_nbr), ar.at<int>(ph.acc_fine), ar.at<int>(ph.acc_cpos),
+                              ph.n_acc, unodes, 0, nullptr, bs->d_err, s));
+      if (bs->correction)
+        RUN(launch_cf_interp<R>(N, unodes, ar.at<int>(ph.cor_nbr), ar.at<int>(ph.cor_fine), ar.at<int>(ph.cor_cpos),
+                                ph.n_cor, fwork, 1, ar.at<double>(ph.cor_ih2), bs->d_err, s));
+    }
+  }
+#undef RUN
+  return cudaSuccess;
+}
+
+void collect_times(flgf_blockset* bs) {
+  if (!bs->ev_pending) return;
+  cudaStreamSynchronize(bs->ctx->stream);
+  for (size_t i = 0; i < bs->ev_used; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, bs->ev[i].second.first, bs->ev[i].second.second) == cudaSuccess)
+      bs->stage_ms[bs->ev[i].first] += ms;
+  }
+  bs->timed_solves++;
+  bs->ev_pending = false;
+}
+
+}  // namespace
+
+extern "C" int flgf_set_option(flgf_blockset* bs, int key, int value) {
+  if (!bs) return FLGF_EINVAL;
+  flgf_ctx* ctx = bs->ctx;
+  switch (key) {
+    case FLGF_OPT_CORRECTION:
+      bs->correction = value != 0;
+      break;
+    case FLGF_OPT_GRAPH:
+      if (value && ctx->stream == nullptr)
+        return fail(ctx, FLGF_EINVAL, "graph capture needs a non-default stream");
+      bs->use_graph = value != 0;
+      break;
+    case FLGF_OPT_TIMING:
+      bs->timing = value != 0;
+      break;
+    default:
+      return fail(ctx, FLGF_EINVAL, "unknown option");
+  }
+  // any change invalidates a captured graph
+  if (bs->gexec) {
+    cudaGraphExecDestroy(bs->gexec);
+    bs->gexec = nullptr;
+  }
+  return FLGF_OK;
+}
+
+extern "C" int flgf_solve(flgf_blockset* bs) {
+  if (!bs) return FLGF_EINVAL;
+  flgf_ctx* ctx = bs->ctx;
+  collect_times(bs);
+  cudaError_t e;
+  if (bs->use_graph) {
+    if (!bs->gexec) {
+      bs->ev_used = 0;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      e = ctx->prec == FLGF_FP64 ? enqueue_solve<double>(bs) : enqueue_solve<float>(bs);
+      cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(ctx, FLGF_ECUDA, std::string("solve capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+      e = cudaGraphInstantiate(&bs->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(ctx, FLGF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    CK(cudaGraphLaunch(bs->gexec, ctx->stream));
+  } else {
+    bs->ev_used = 0;
+    e = ctx->prec == FLGF_FP64 ? enqueue_solve<double>(bs) : enqueue_solve<float>(bs);
+    if (e != cudaSuccess) return fail(ctx, FLGF_ECUDA, std::string("solve: ") + cudaGetErrorString(e));
+  }
+  bs->ev_pending = bs->timing && bs->ev_used > 0;
+  bs->solved = true;
+  return FLGF_OK;
+}
+
+extern "C" int flgf_stage_times(flgf_blockset* bs, double* ms, int n_stages, int* n_solves, int reset) {
+  if (!bs || n_stages < 0 || n_stages > 7 || (n_stages > 0 && !ms)) return FLGF_EINVAL;
+  collect_times(bs);
+  for (int i = 0; i < n_stages; ++i) ms[i] = bs->stage_ms[i];
+  if (n_solves) *n_solves = bs->timed_solves;
+  if (reset) {
+    for (double& v : bs->stage_ms) v = 0.0;
+    bs->timed_solves = 0;
+  }
+  return FLGF_OK;
+}
+
+extern "C" int flgf_get_potential(flgf_blockset* bs, int problem, int level, void* u, int where) {
+  if (!bs || !u || (where != FLGF_HOST && where != FLGF_DEVICE)) return FLGF_EINVAL;
+  flgf_ctx* ctx = bs->ctx;
+  if (check_pl(bs, problem, level) != FLGF_OK) return fail(ctx, FLGF_EINVAL, "get_potential: bad problem/level");
+  if (!bs->solved) return fail(ctx, FLGF_ESTATE, "get_potential before solve");
+  const LevelInfo& L = bs->prob[problem].lev[level];
+  const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4, N3 = (size_t)ctx->N * ctx->N * ctx->N;
+  CK(cudaMemcpyAsync(u, (char*)bs->unodes + rs * N3 * L.ugid0, rs * N3 * L.c.size(), kind(where, false), ctx->stream));
+  if (where == FLGF_HOST) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, bs->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return fail(ctx, FLGF_EDEVICE, "a coarse-fine interpolation met a missing halo block");
+  }
+  return FLGF_OK;
+}
+
+extern "C" int flgf_laplacian(flgf_blockset* bs, int problem, int level, const void* u, void* out, int where) {
+  if (!bs || !u || !out || (where != FLGF_HOST && where != FLGF_DEVICE)) return FLGF_EINVAL;
+  flgf_ctx* ctx = bs->ctx;
+  if (check_pl(bs, problem, level) != FLGF_OK) return fail(ctx, FLGF_EINVAL, "laplacian: bad problem/level");
+  const LevelInfo& L = bs->prob[problem].lev[level];
+  const int N = ctx->N;
+  const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4, N3 = (size_t)N * N * N, bytes = rs * N3 * L.c.size();
+  const void* din = u;
+  void* dout = out;
+  if (where == FLGF_HOST) {
+    CK(cudaMemcpyAsync(bs->lap_in, u, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    din = bs->lap_in;
+    dout = bs->lap_out;
+  }
+  const double ih2 = 1.0 / (L.h * L.h);
+  cudaError_t e = ctx->prec == FLGF_FP64
+                      ? launch_laplacian<double>(N, (const double*)din, bs->ar.at<int>(L.nbr6_off), (int)L.c.size(), ih2,
+                                                 (double*)dout, ctx->stream)
+                      : launch_laplacian<float>(N, (const float*)din, bs->ar.at<int>(L.nbr6_off), (int)L.c.size(), ih2,
+                                                (float*)dout, ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, FLGF_ECUDA, std::string("laplacian: ") + cudaGetErrorString(e));
+  if (where == FLGF_HOST) {
+    CK(cudaMemcpyAsync(out, bs->lap_out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return FLGF_OK;
+}

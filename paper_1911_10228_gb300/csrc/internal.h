@@ -1,0 +1,82 @@
+// Internal launcher interface between the host orchestration (flgf_api.cu)
+// and the kernels (lgf.cu, fft.cu, hadamard.cu, stencil.cu).  Not part of the
+// public C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace flgf {
+
+// ---- a0: LGF table and kernel arrays (lgf.cu) ----------------------------
+// Bessel table B[k][j] = ive(k, 2 t_j), k = 0..K, j over the exp-sinh nodes.
+cudaError_t launch_bessel_table(double* B, int K, cudaStream_t s);
+int quad_nodes();
+// Canonical LGF table T[n1][n2][n3] (0 <= n3 <= n2 <= n1 <= R, n1^2+n2^2+n3^2 <= R^2).
+cudaError_t launch_lgf_table(const double* B, int K, double* table, int R, cudaStream_t s);
+// LGF at integer points pts[i] (x3) with the table / A^3 / A^2 switch.
+cudaError_t launch_lgf_eval(const double* table, int R, double rt, double ra, const int32_t* pts,
+                            int n, double* out, cudaStream_t s);
+// (2N)^3 circular kernel arrays for octree level k, every offset d in [-3,3]^3:
+// out[d][i0][i1][i2] = G(2^k (N d + Delta)), Delta = i (i < N) or i - 2N (i > N), 0 at i == N.
+cudaError_t launch_kernel_arrays(const double* table, int R, double rt, double ra, int N, int k,
+                                 double* out, cudaStream_t s);
+
+// ---- a2/a4 FFTs (fft.cu) ---------------------------------------------------
+cudaError_t fft_init_constants();
+// Forward R2C of zero-padded N^3 blocks: in[gid_list[i]] -> spec column sid_list[i].
+template <typename R>
+cudaError_t launch_fft_forward(int N, const R* nodes, const int* gids, const int* sids, int count,
+                               void* spec, int spec_blocks, cudaStream_t s);
+// Inverse C2R, keep the first N^3 outputs, scale by scale[i]/(2N)^3, write (or add) to out[gids[i]].
+template <typename R>
+cudaError_t launch_fft_inverse(int N, const void* acc, int spec_blocks, const int* sids, const int* gids,
+                               const double* scales, int count, R* out, cudaStream_t s);
+// Kernel spectra of one octree level from the (2N)^3 kernel arrays (FP64 FFT),
+// stored as [chunk][343][T] in precision R.
+template <typename R>
+cudaError_t launch_kernel_spectra(int N, const double* karr, void* kspec_level, double* tmp, cudaStream_t s);
+
+// ---- a3 spectrum multiply-accumulate (hadamard.cu) ------------------------
+struct HadTile {
+  int src_off;      // offset into src id array; region cells (2 Rx)(2 Ry)(2 Rz), last axis fastest
+  int tgt_off;      // offset into tgt id array; (2 Px)(2 Py)(2 Pz) target cells
+  int level;        // octree level k (selects the kernel spectra)
+  int excl_near;    // 1 when near neighbours are not part of this level's lists
+  int p0[3];        // tile parent box origin (parent coords)
+  int P[3];         // tile parent box dims
+  int r0[3];        // region parent box origin
+  int Rg[3];        // region parent box dims
+};
+template <typename R>
+cudaError_t launch_hadamard(int N, const HadTile* tiles, int ntiles, int max_parents, int max_region_cells,
+                            const int* src_ids, const int* tgt_ids, const void* spec, void* acc,
+                            int spec_blocks, const void* kspec, size_t kspec_level_stride,
+                            cudaStream_t s);
+
+// ---- a1/a5 and multi-resolution stencils (stencil.cu) ----------------------
+// J1: dense 1-D Lagrange matrix [2N][N] (row = child node of the two children, column = parent node).
+template <typename R>
+cudaError_t launch_anterp(int N, const double* J1, const int* parents, const int* children /*[n][8]*/, int n,
+                          R* nodes, cudaStream_t s);
+template <typename R>
+cudaError_t launch_interp_add(int N, const double* J1, const int* childs, const int* parents, const int* cpos,
+                              int n, R* unodes, cudaStream_t s);
+// dst[dst_ids[i]] = src[src_ids[i]] * (mask? mask[i] : 1)
+template <typename R>
+cudaError_t launch_copy_blocks(int N, const R* src, const int* src_ids, R* dst, const int* dst_ids,
+                               const uint8_t* zero, int n, cudaStream_t s);
+// Coarsening: out[coarse[i]] = mean of 8 fine cells of children fine[i][8]
+template <typename R>
+cudaError_t launch_coarsen(int N, const R* fine_f, const int* fine_ids, R* coarse_f, const int* coarse_ids,
+                           int n, cudaStream_t s);
+// Coarse-fine quadratic interpolation from level l to level l+1 blocks.
+// nbr27[i][27]: coarse block ids of the parent's 3x3x3 neighbourhood (-1 if absent);
+// mode 0: ufine[fine[i]] += J u_coarse; mode 1: ffine[fine[i]] -= L^{(hf)} J u_coarse, inv_hf2[i] = 1/hf^2.
+template <typename R>
+cudaError_t launch_cf_interp(int N, const R* ucoarse, const int* nbr27, const int* fine_ids, const int* cpos,
+                             int n, R* fine, int mode, const double* inv_hf2, int* err_flag, cudaStream_t s);
+// 7-point Laplacian with same-level face neighbours nbr6[i][6] (-1 absent -> 0 output).
+template <typename R>
+cudaError_t launch_laplacian(int N, const R* u, const int* nbr6, int n, double inv_h2, R* out, cudaStream_t s);
+
+}  // namespace flgf
