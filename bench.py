@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the FLGF Poisson solve (arXiv:1911.10228) on one GB300.
+
+Workload: the 256^3 uniform lattice as 16^3 blocks of 16^3 cells, octree
+levels 0..2 (+ root), Lagrange n_I = 6, source = 16 seeded Gaussians (sigma
+3-10 cells, centres in the inner 128^3 region, amplitudes U(-1, 1)).  One
+step = one full solve (anterpolation, forward FFTs, spectrum MAC, inverse
+FFTs, interpolation) with the source already resident in HBM; L2 is flushed
+(256 MB write) before every timed step.  The headline value is the FP32
+form's DoF/s; the plain FP64 solve is timed on the same GPU beside it and
+both are checked against the FP64 CPU oracle on sampled target blocks.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank solves its own replica (the workload does
+not shard without a halo exchange); value = all ranks' DoF / max rank time.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson DoF/s at stated rel err: FP32 batched vs FP64 plain; % HBM roofline"
+WORKLOAD = ("uniform 256^3 lattice, 16^3 blocks of 16^3 cells, octree levels 0-2 + root, n_I=6, "
+            "16 Gaussians sigma 3-10 cells in the inner 128^3, seed 0")
+N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_ALU_PEAK_TFLOPS = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
+FP64_NOMINAL_TFLOPS = 1.25
+FALLBACK_HBM_GBS = 6800.0
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=24, help="target blocks in the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if key in d:
+                return float(d[key]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def file_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel_src: str, kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = file_sha(os.path.join(ROOT, "paper_1911_10228_gb300", "csrc", kernel_src))
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+            if kv.get("kernel") == kernel and kv.get("src_sha") == sha and kv.get("workload") == "uniform256":
+                return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+def oracle_sample(prob, n_sample: int, seed: int = 0):
+    """FP64 oracle on a sample of target blocks; returns (targets, u_on_targets, seconds, setup_seconds)."""
+    from oracle.flgf import FLGF
+    from oracle.lgf import LGF
+    t0 = time.perf_counter()
+    op = FLGF(LGF(), prob.coords[0], prob.N, 6)
+    for k in range(op.tree.top + 1):
+        for d in np.ndindex(7, 7, 7):
+            op.kernel_spectrum(k, np.array(d) - 3)
+    setup = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    nz = np.nonzero(np.any(prob.f[0] != 0, axis=(1, 2, 3)))[0]
+    targets = np.sort(rng.choice(nz, size=min(n_sample, nz.size), replace=False))
+    t1 = time.perf_counter()
+    u = op.apply(prob.f[0], h=prob.h0, targets=targets)
+    dt = time.perf_counter() - t1
+    return targets, u[targets], dt, setup, op
+
+
+def run_reference(a, rank, world):
+    """The oracle arm: FP64 CPU oracle on bounded samples of the workload."""
+    if rank != 0:
+        return
+    from paper_1911_10228_gb300.inputs import config_uniform_256
+    prob = config_uniform_256()
+    from oracle.flgf import FLGF
+    from oracle.lgf import LGF
+    op = FLGF(LGF(), prob.coords[0], prob.N, 6)
+    for k in range(op.tree.top + 1):
+        for d in np.ndindex(7, 7, 7):
+            op.kernel_spectrum(k, np.array(d) - 3)
+    rng = np.random.default_rng(1)
+    nz = np.nonzero(np.any(prob.f[0] != 0, axis=(1, 2, 3)))[0]
+    per_step = 2
+    times = []
+    for i in range(a.warmup + a.steps):
+        tg = np.sort(rng.choice(nz, per_step, replace=False))
+        t = time.perf_counter()
+        op.apply(prob.f[0], h=prob.h0, targets=tg)
+        if i >= a.warmup:
+            times.append(time.perf_counter() - t)
+    ms = 1e3 * float(np.mean(times))
+    dof = per_step * prob.N ** 3
+    value = dof / (ms / 1e3)
+    cores = os.cpu_count()
+    sample = f"{per_step} of 4096 target blocks per step (full upward and downward passes, all levels)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": 16, "n_interp": 6, "blocks": 4096, "dof": prob.dof(),
+                   "parallelism": "oracle on host cores"},
+        "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(a, rank, world, dist):
+    import torch
+
+    from paper_1911_10228_gb300 import flgf as F
+    from paper_1911_10228_gb300.inputs import config_uniform_256
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    prob = config_uniform_256()
+    N = prob.N
+    dof = prob.dof()
+    f64 = torch.as_tensor(prob.f[0])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    res = {}
+    for prec in ("fp32", "fp64"):
+        ctx = F.Context(N=N, n_interp=6, precision=prec)
+        bs = F.BlockSet(ctx, [prob.coords], [prob.h0])
+        bs.load_source(0, 0, f64.to("cuda"))
+        for _ in range(a.warmup):
+            bs.solve()
+        torch.cuda.synchronize()
+        bs.set_option(F.OPT_TIMING, 1)
+        bs.stage_times(reset=True)
+        steps = a.steps if prec == "fp32" else max(3, min(a.steps, 10))
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if dist:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(dev)
+        with sampler:
+            for s0, s1 in evs:
+                with torch.cuda.stream(ctx.stream):
+                    flush.zero_()
+                s0.record(ctx.stream)
+                bs.solve()
+                s1.record(ctx.stream)
+            torch.cuda.synchronize()
+        if dist:
+            torch.distributed.barrier()
+        step_ms = [s0.elapsed_time(s1) for s0, s1 in evs]
+        total = torch.tensor([sum(step_ms)], dtype=torch.float64, device="cuda")
+        if dist:
+            torch.distributed.all_reduce(total, op=torch.distributed.ReduceOp.MAX)
+        stage, n_timed = bs.stage_times(reset=True)
+        bs.set_option(F.OPT_TIMING, 0)
+        res[prec] = {
+            "ms_per_step": float(total.item()) / steps, "steps": steps, "launches": bs.launch_count(),
+            "stages_ms": {k: v / max(n_timed, 1) for k, v in stage.items()}, "clocks": sampler.summary(),
+            "work": bs.work_counts(), "ctx": ctx, "bs": bs,
+        }
+        res[prec]["u"] = bs.potential(0, 0).double().cpu().numpy()
+
+    # end-to-end FP32 through the public API with pinned host buffers
+    r32 = res["fp32"]
+    bs = r32["bs"]
+    ctx = r32["ctx"]
+    h_src = torch.empty(tuple(f64.shape), dtype=torch.float32, pin_memory=True)
+    h_src.copy_(f64.float())
+    h_out = torch.empty_like(h_src, pin_memory=True)
+    e2e_ms = []
+    for i in range(a.warmup + a.steps):
+        t = time.perf_counter()
+        bs.load_source(0, 0, h_src)
+        bs.solve()
+        bs.potential_host(0, 0, out=h_out.numpy())
+        if i >= a.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t))
+    e2e = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device="cuda")
+    if dist:
+        torch.distributed.all_reduce(e2e, op=torch.distributed.ReduceOp.MAX)
+    e2e_ms_step = float(e2e.item()) / a.steps
+    nbytes = h_src.numel() * 4
+
+    # accuracy and CPU baseline against the FP64 oracle (rank 0, one GPU only)
+    acc, cpu = None, None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        targets, u_ref, dt, setup, _ = oracle_sample(prob, a.cpu_sample)
+        def errs(u):
+            d = u[targets] - u_ref
+            return {"linf": float(np.max(np.abs(d)) / np.max(np.abs(u_ref))),
+                    "l2": float(np.linalg.norm(d) / np.linalg.norm(u_ref))}
+        acc = {"fp32_vs_oracle": errs(res["fp32"]["u"]), "fp64_vs_oracle": errs(res["fp64"]["u"]),
+               "sample": f"{len(targets)} of 4096 target blocks (seeded), FP64 oracle"}
+        cpu = {"value": len(targets) * N ** 3 / dt, "unit": "DoF/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{len(targets)} of 4096 target blocks with full upward/downward passes; "
+                         f"{dt:.1f} s solve, {setup:.1f} s LGF/kernel-spectrum setup excluded"}
+
+    hbm, hbm_src = peaks()
+    NW = 2 * N * 2 * N * (N + 1)
+    rows = {}
+    for prec, rs in (("fp32", 4), ("fp64", 8)):
+        r = res[prec]
+        w = r["work"]
+        mac_ms = r["stages_ms"]["spectrum_mac"]
+        flops = w["pairs"] * NW * 8.0
+        fwd_bytes = w["fwd_ffts"] * (N ** 3 * rs + NW * 2 * rs)
+        inv_bytes = w["inv_ffts"] * (N ** 3 * rs + NW * 2 * rs)
+        rows[prec] = {
+            "mac_tflops": flops / (mac_ms / 1e3) / 1e12 if mac_ms > 0 else None,
+            "fft_fwd_gbs": fwd_bytes / (r["stages_ms"]["fft_forward"] / 1e3) / 1e9,
+            "fft_inv_gbs": inv_bytes / (r["stages_ms"]["fft_inverse"] / 1e3) / 1e9,
+            "mac_flops": flops,
+        }
+    ach = rows["fp32"]["mac_tflops"]
+    line = {
+        "metric": METRIC,
+        "value": dof * world / (res["fp32"]["ms_per_step"] / 1e3),
+        "unit": "DoF/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": res["fp32"]["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "n_interp": 6, "blocks": 4096, "dof": dof,
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "rel_err": acc,
+        "fp64_plain": {"value": dof * world / (res["fp64"]["ms_per_step"] / 1e3), "unit": "DoF/s",
+                       "ms_per_step": res["fp64"]["ms_per_step"], "steps": res["fp64"]["steps"],
+                       "stages_ms": res["fp64"]["stages_ms"],
+                       "spectrum_mac_tflops": rows["fp64"]["mac_tflops"],
+                       "spectrum_mac_frac_of_fp64_nominal": (rows["fp64"]["mac_tflops"] or 0) / FP64_NOMINAL_TFLOPS},
+        "roofline": {"bound": "alu", "kernel": "hadamard_kernel<float,2> (spectrum MAC, a3)",
+                     "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (ach / FP32_ALU_PEAK_TFLOPS) if ach else None,
+                     "traffic": ncu_traffic("hadamard.cu", "hadamard_kernel"),
+                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+                     "flops_per_launch": rows["fp32"]["mac_flops"]},
+        "hbm_kernels": {"peak_gbs": hbm, "peak_source": hbm_src,
+                        "fft_forward_gbs": rows["fp32"]["fft_fwd_gbs"],
+                        "fft_forward_frac": rows["fp32"]["fft_fwd_gbs"] / hbm,
+                        "fft_inverse_gbs": rows["fp32"]["fft_inv_gbs"],
+                        "fft_inverse_frac": rows["fp32"]["fft_inv_gbs"] / hbm},
+        "stages_ms": res["fp32"]["stages_ms"],
+        "cpu_baseline": cpu,
+        "e2e": {"value": dof * world / (e2e_ms_step / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms_step},
+        "gpu_launches": res["fp32"]["launches"] * a.steps,
+        "clocks": res["fp32"]["clocks"],
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    for prec in res:
+        res[prec]["bs"].close()
+        res[prec]["ctx"].close()
+
+
+def main():
+    a = args_parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = world > 1
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if dist:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    run_ours(a, rank, world, dist)
+    if dist:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -157,6 +157,10 @@ int flgf_stage_times(flgf_blockset* bs, double* ms, int n_stages, int* n_solves,
 int flgf_work_counts(const flgf_blockset* bs, int64_t* pairs, int64_t* fwd_ffts, int64_t* inv_ffts,
                      int64_t* kernel_offsets);
 
+/* Number of kernels the last flgf_solve enqueued (one per launch; a replayed
+ * CUDA graph launches the same kernels as the solve it captured). */
+int64_t flgf_launch_count(const flgf_blockset* bs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,15 +17,19 @@ parent that are not neighbours of B; at the top level: every block that is
 not a neighbour.  Every (target, source) pair of finest blocks is then
 handled exactly once.
 
-Interpolation nodes (reading of the method of the FLGF paper it builds on,
-which this paper does not restate): the N^3 nodes of a level-k block are the
-lattice points at stride 2^k, so the level-k kernel between node p of block t
-and node q of block s is the exact LGF value G(2^k (N (t - s) + p - q)).
-Along one axis the two children of a parent carry 2N nodes at positions
-0..2N-1 and the parent's N nodes sit at positions 0, 2, ..., 2N-2.
-J_1 (2N x N): even child nodes copy the coinciding parent node; odd child
-nodes use n_I-point Lagrange interpolation on the nearest parent nodes
-(window centred, shifted inwards at the block faces).  The regularisation
+Interpolation nodes (reading; the paper defers the FMM details to the FLGF
+paper it builds on): every octree node is a Cartesian block of N^3 cells
+(Sec. 2.1) and field values live at cell centres (Sec. 3), so the N^3 nodes
+of a level-k block are the centres of its N^3 cells of width 2^k.  Node
+differences are then multiples of 2^k lattice spacings and the level-k kernel
+between node p of block t and node q of block s is the exact LGF value
+G(2^k (N (t - s) + p - q)).  Along one axis, in units of the child spacing,
+the 2N nodes of two sibling children sit at j + 1/2 (j = 0..2N-1) and the N
+nodes of their parent at 2p + 1 (p = 0..N-1): no node coincides (staggered
+as in Sec. 3).  J_1 (2N x N) interpolates each child node with n_I-point
+Lagrange polynomials on the parent nodes nearest to it (window centred,
+shifted inwards at the block faces, so the first and last child nodes are
+extrapolated by a quarter of the parent spacing).  The regularisation
 (anterpolation) operator is its adjoint, R = J^T.  The 3-D operators are
 tensor products.
 
@@ -119,20 +123,23 @@ class Octree:
 
 
 def lagrange_J1(N: int, n_interp: int) -> np.ndarray:
-    """1-D parent-to-children interpolation matrix J_1 (2N x N)."""
+    """1-D parent-to-children interpolation matrix J_1 (2N x N), cell-centred nodes."""
     if not (1 <= n_interp <= N):
         raise ValueError("need 1 <= n_I <= N")
     J = np.zeros((2 * N, N))
+    parent = 2.0 * np.arange(N) + 1.0
     for j in range(2 * N):
-        if j % 2 == 0:
-            J[j, j // 2] = 1.0
-            continue
-        start = (j + 1) // 2 - n_interp // 2
+        x = j + 0.5
+        if n_interp % 2 == 0:
+            lo = int(np.floor((x - 1.0) / 2.0))        # parent node just left of x
+            start = lo - (n_interp // 2 - 1)
+        else:
+            start = int(np.argmin(np.abs(parent - x))) - n_interp // 2
         start = min(max(start, 0), N - n_interp)
-        nodes = 2.0 * (start + np.arange(n_interp))
+        nodes = parent[start:start + n_interp]
         for m in range(n_interp):
             others = np.delete(nodes, m)
-            J[j, start + m] = np.prod((j - others) / (nodes[m] - others))
+            J[j, start + m] = np.prod((x - others) / (nodes[m] - others))
     return J
 
 

@@ -47,26 +47,32 @@ inline uint64_t key3(int a, int b, int c) {
 }
 inline uint64_t key3(const I3& v) { return key3(v[0], v[1], v[2]); }
 
-// 1-D Lagrange interpolation from the N parent nodes (positions 0, 2, ..,
-// 2N-2) to the 2N nodes of the two children (positions 0..2N-1): even rows
-// copy the coinciding node; odd rows interpolate on n_I consecutive nodes
-// centred on the point and shifted inwards at the faces (Sec. 2.1).
+// 1-D Lagrange interpolation between octree levels (Sec. 2.1).  A level-k
+// block's nodes are the centres of its N cells: in units of the child
+// spacing the 2N nodes of two sibling children lie at j + 1/2 and the N
+// parent nodes at 2p + 1.  Each child node takes the n_I parent nodes nearest
+// to it (window centred on it, moved inwards at the faces).
 std::vector<double> lagrange_matrix(int N, int nI) {
   std::vector<double> J((size_t)2 * N * N, 0.0);
   for (int j = 0; j < 2 * N; ++j) {
-    if (j % 2 == 0) {
-      J[(size_t)j * N + j / 2] = 1.0;
-      continue;
+    const double x = j + 0.5;
+    int start;
+    if (nI % 2 == 0) {
+      start = (int)std::floor((x - 1.0) / 2.0) - (nI / 2 - 1);
+    } else {
+      int best = 0;
+      for (int p = 1; p < N; ++p)
+        if (std::fabs(2.0 * p + 1.0 - x) < std::fabs(2.0 * best + 1.0 - x)) best = p;
+      start = best - nI / 2;
     }
-    int start = (j + 1) / 2 - nI / 2;
     start = std::min(std::max(start, 0), N - nI);
     for (int m = 0; m < nI; ++m) {
-      const double xm = 2.0 * (start + m);
+      const double xm = 2.0 * (start + m) + 1.0;
       double w = 1.0;
       for (int q = 0; q < nI; ++q)
         if (q != m) {
-          const double xq = 2.0 * (start + q);
-          w *= ((double)j - xq) / (xm - xq);
+          const double xq = 2.0 * (start + q) + 1.0;
+          w *= (x - xq) / (xm - xq);
         }
       J[(size_t)j * N + start + m] = w;
     }
@@ -159,6 +165,7 @@ struct flgf_blockset {
   double stage_ms[7] = {0, 0, 0, 0, 0, 0, 0};
   int timed_solves = 0;
   bool ev_pending = false;
+  int64_t launches = 0;  // kernels enqueued by the last solve
 };
 
 // ----------------------------------------------------------------------------
@@ -755,6 +762,8 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
 
 extern "C" int64_t flgf_blockset_dof(const flgf_blockset* bs) { return bs ? bs->dof : -1; }
 
+extern "C" int64_t flgf_launch_count(const flgf_blockset* bs) { return bs ? bs->launches : -1; }
+
 extern "C" int flgf_work_counts(const flgf_blockset* bs, int64_t* pairs, int64_t* fwd, int64_t* inv, int64_t* koff) {
   if (!bs) return FLGF_EINVAL;
   if (pairs) *pairs = bs->pairs;
@@ -830,12 +839,18 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
   cudaError_t e;
 #define RUN(x)                              \
   if ((e = (x)) != cudaSuccess) return e;
+#define KRUN(n, x)                              \
+  do {                                          \
+    if ((n) > 0) bs->launches++;                \
+    if ((e = (x)) != cudaSuccess) return e;     \
+  } while (0)
+  bs->launches = 0;
   RUN(cudaMemcpyAsync(fwork, bs->fuser, sizeof(R) * N3 * bs->B, cudaMemcpyDeviceToDevice, s));
   {
     StageScope sc(bs, 0);
     for (int l = bs->Lmax - 2; l >= 0; --l) {
       const PhaseOff& ph = bs->ph[l];
-      RUN(launch_coarsen<R>(N, fwork, ar.at<int>(ph.crs_fine), fwork, ar.at<int>(ph.crs_coarse), ph.n_crs, s));
+      KRUN(ph.n_crs, launch_coarsen<R>(N, fwork, ar.at<int>(ph.crs_fine), fwork, ar.at<int>(ph.crs_coarse), ph.n_crs, s));
     }
   }
   for (int l = 0; l < bs->Lmax; ++l) {
@@ -843,42 +858,43 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
     const int maxtop = (int)ph.n_ant.size() - 1;
     {
       StageScope sc(bs, 1);
-      RUN(launch_copy_blocks<R>(N, fwork, ar.at<int>(ph.prep_src), nodes, ar.at<int>(ph.prep_dst),
+      KRUN(ph.n_prep, launch_copy_blocks<R>(N, fwork, ar.at<int>(ph.prep_src), nodes, ar.at<int>(ph.prep_dst),
                                 ar.at<uint8_t>(ph.prep_zero), ph.n_prep, s));
       for (int k = 1; k <= maxtop; ++k)
-        RUN(launch_anterp<R>(N, c->d_J1, ar.at<int>(ph.ant_par[k]), ar.at<int>(ph.ant_ch[k]), ph.n_ant[k], nodes, s));
+        KRUN(ph.n_ant[k], launch_anterp<R>(N, c->d_J1, ar.at<int>(ph.ant_par[k]), ar.at<int>(ph.ant_ch[k]), ph.n_ant[k], nodes, s));
     }
     {
       StageScope sc(bs, 2);
-      RUN(launch_fft_forward<R>(N, nodes, ar.at<int>(ph.fwd_gid), ar.at<int>(ph.fwd_sid), ph.n_fwd, bs->spec,
+      KRUN(ph.n_fwd, launch_fft_forward<R>(N, nodes, ar.at<int>(ph.fwd_gid), ar.at<int>(ph.fwd_sid), ph.n_fwd, bs->spec,
                                 ph.nblocks, s));
     }
     {
       StageScope sc(bs, 3);
-      RUN(launch_hadamard<R>(N, ar.at<HadTile>(ph.tiles), ph.n_tiles, ph.max_par, ph.max_cells, ar.at<int>(ph.src_ids),
+      KRUN(ph.n_tiles, launch_hadamard<R>(N, ar.at<HadTile>(ph.tiles), ph.n_tiles, ph.max_par, ph.max_cells, ar.at<int>(ph.src_ids),
                              ar.at<int>(ph.tgt_ids), bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
     }
     {
       StageScope sc(bs, 4);
-      RUN(launch_fft_inverse<R>(N, bs->acc, ph.nblocks, ar.at<int>(ph.inv_sid), ar.at<int>(ph.inv_gid),
+      KRUN(ph.n_inv, launch_fft_inverse<R>(N, bs->acc, ph.nblocks, ar.at<int>(ph.inv_sid), ar.at<int>(ph.inv_gid),
                                 ar.at<double>(ph.inv_scale), ph.n_inv, unodes, s));
     }
     {
       StageScope sc(bs, 5);
       for (int k = maxtop - 1; k >= 0; --k)
-        RUN(launch_interp_add<R>(N, c->d_J1, ar.at<int>(ph.itp_ch[k]), ar.at<int>(ph.itp_par[k]),
+        KRUN(ph.n_itp[k], launch_interp_add<R>(N, c->d_J1, ar.at<int>(ph.itp_ch[k]), ar.at<int>(ph.itp_par[k]),
                                  ar.at<int>(ph.itp_cpos[k]), ph.n_itp[k], unodes, s));
     }
     {
       StageScope sc(bs, 6);
-      RUN(launch_copy_blocks<R>(N, unodes, ar.at<int>(ph.sel_src), unodes, ar.at<int>(ph.sel_dst), nullptr, ph.n_sel, s));
-      RUN(launch_cf_interp<R>(N, unodes, ar.at<int>(ph.acc_nbr), ar.at<int>(ph.acc_fine), ar.at<int>(ph.acc_cpos),
+      KRUN(ph.n_sel, launch_copy_blocks<R>(N, unodes, ar.at<int>(ph.sel_src), unodes, ar.at<int>(ph.sel_dst), nullptr, ph.n_sel, s));
+      KRUN(ph.n_acc, launch_cf_interp<R>(N, unodes, ar.at<int>(ph.acc_nbr), ar.at<int>(ph.acc_fine), ar.at<int>(ph.acc_cpos),
                               ph.n_acc, unodes, 0, nullptr, bs->d_err, s));
       if (bs->correction)
-        RUN(launch_cf_interp<R>(N, unodes, ar.at<int>(ph.cor_nbr), ar.at<int>(ph.cor_fine), ar.at<int>(ph.cor_cpos),
+        KRUN(ph.n_cor, launch_cf_interp<R>(N, unodes, ar.at<int>(ph.cor_nbr), ar.at<int>(ph.cor_fine), ar.at<int>(ph.cor_cpos),
                                 ph.n_cor, fwork, 1, ar.at<double>(ph.cor_ih2), bs->d_err, s));
     }
   }
+#undef KRUN
 #undef RUN
   return cudaSuccess;
 }

@@ -62,6 +62,7 @@ PROTOTYPES = {
     "flgf_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "flgf_stage_times": (ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, ctypes.c_int, _c_int_p, ctypes.c_int]),
     "flgf_work_counts": (ctypes.c_int, [ctypes.c_void_p, _c_i64_p, _c_i64_p, _c_i64_p, _c_i64_p]),
+    "flgf_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
 }
 
 _LIB = None
@@ -183,6 +184,10 @@ class BlockSet:
         v = [ctypes.c_int64() for _ in range(4)]
         self.ctx.check(self.lib.flgf_work_counts(self.handle, *[ctypes.byref(x) for x in v]), "flgf_work_counts")
         return dict(zip(("pairs", "fwd_ffts", "inv_ffts", "kernel_offsets"), (x.value for x in v)))
+
+    def launch_count(self) -> int:
+        """Kernels enqueued by the last solve."""
+        return int(self.lib.flgf_launch_count(self.handle))
 
     def nblk(self, problem: int, level: int) -> int:
         return self.levels[problem][level].shape[0]

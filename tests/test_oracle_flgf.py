@@ -7,18 +7,33 @@ from oracle.flgf import FLGF, Octree, blocks_to_dense, dense_to_blocks, lagrange
 from paper_1911_10228_gb300.inputs import box_coords, config_plain_32
 
 
-@pytest.mark.parametrize("N,nI", [(8, 6), (16, 6), (8, 4), (16, 10)])
+@pytest.mark.parametrize("N,nI", [(8, 6), (16, 6), (8, 4), (16, 10), (8, 5)])
 def test_lagrange_reproduces_polynomials(N, nI):
-    """Lagrange interpolation on n_I nodes is exact for degree < n_I."""
+    """Lagrange interpolation on n_I nodes is exact for degree < n_I
+    (child nodes at j + 1/2, parent nodes at 2p + 1)."""
     J = lagrange_J1(N, nI)
-    xc = np.arange(2 * N, dtype=np.float64)       # child node positions
-    xp = 2.0 * np.arange(N)                       # parent node positions
+    xc = np.arange(2 * N) + 0.5
+    xp = 2.0 * np.arange(N) + 1.0
     for deg in range(nI):
         p = lambda x: ((x - 7.3) / N) ** deg
         assert np.max(np.abs(J @ p(xp) - p(xc))) < 1e-11 * max(1.0, np.max(np.abs(p(xc))))
-    # interior odd rows carry the symmetric centred 6-point weights
-    if nI == 6:
-        assert np.allclose(J[7, 1:7] * 256.0, [3, -25, 150, 150, -25, 3])
+    # mirror symmetry of the node layout: J[2N-1-j, N-1-p] = J[j, p]
+    assert np.allclose(J[::-1, ::-1], J, rtol=0, atol=1e-14)
+    # each child row uses n_I consecutive parent nodes
+    assert np.all(np.count_nonzero(np.abs(J) > 0, axis=1) <= nI)
+
+
+def test_lagrange_interior_weights_quarter_offset():
+    """Interior child nodes sit a quarter parent spacing from the nearest parent
+    node; the centred 6-point weights are the Lagrange basis at +1/4 on nodes
+    at -5/2 .. 5/2 (units of the parent spacing), written out independently here."""
+    J = lagrange_J1(16, 6)
+    w = J[10, 2:8]  # child x = 10.5 between parent nodes 9 (p = 4) and 11 (p = 5)
+    t = np.array([-2.5, -1.5, -0.5, 0.5, 1.5, 2.5]) * 2.0  # node offsets from x' = 10 (child units)
+    xq = 0.5                                             # child at 10.5 relative to 10
+    ref = [np.prod([(xq - t[q]) / (t[m] - t[q]) for q in range(6) if q != m]) for m in range(6)]
+    assert np.allclose(w, ref, rtol=0, atol=1e-15)
+    assert abs(w.sum() - 1.0) < 1e-15
 
 
 def test_every_pair_handled_once():
