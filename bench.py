@@ -48,8 +48,10 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=24, help="target blocks in the oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=64, help="target blocks in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precisions", default="fp32,fp64", help="contexts to time (profiling runs use fp32)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     return ap.parse_args()
 
 
@@ -208,7 +210,10 @@ def run_ours(a, rank, world, dist):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     res = {}
-    for prec in ("fp32", "fp64"):
+    precs = [p for p in a.precisions.split(",") if p]
+    if "fp32" not in precs:
+        raise SystemExit("the headline value is the FP32 form: --precisions must include fp32")
+    for prec in precs:
         ctx = F.Context(N=N, n_interp=6, precision=prec)
         bs = F.BlockSet(ctx, [prob.coords], [prob.h0])
         bs.load_source(0, 0, f64.to("cuda"))
@@ -254,7 +259,7 @@ def run_ours(a, rank, world, dist):
     h_src.copy_(f64.float())
     h_out = torch.empty_like(h_src, pin_memory=True)
     e2e_ms = []
-    for i in range(a.warmup + a.steps):
+    for i in range(0 if a.no_e2e else a.warmup + a.steps):
         t = time.perf_counter()
         bs.load_source(0, 0, h_src)
         bs.solve()
@@ -264,7 +269,7 @@ def run_ours(a, rank, world, dist):
     e2e = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device="cuda")
     if dist:
         torch.distributed.all_reduce(e2e, op=torch.distributed.ReduceOp.MAX)
-    e2e_ms_step = float(e2e.item()) / a.steps
+    e2e_ms_step = float(e2e.item()) / a.steps if e2e_ms else None
     nbytes = h_src.numel() * 4
 
     # accuracy and CPU baseline against the FP64 oracle (rank 0, one GPU only)
@@ -275,8 +280,9 @@ def run_ours(a, rank, world, dist):
             d = u[targets] - u_ref
             return {"linf": float(np.max(np.abs(d)) / np.max(np.abs(u_ref))),
                     "l2": float(np.linalg.norm(d) / np.linalg.norm(u_ref))}
-        acc = {"fp32_vs_oracle": errs(res["fp32"]["u"]), "fp64_vs_oracle": errs(res["fp64"]["u"]),
-               "sample": f"{len(targets)} of 4096 target blocks (seeded), FP64 oracle"}
+        acc = {p + "_vs_oracle": errs(res[p]["u"]) for p in res}
+        acc.update({
+               "sample": f"{len(targets)} of 4096 target blocks (seeded), FP64 oracle"})
         cpu = {"value": len(targets) * N ** 3 / dt, "unit": "DoF/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{len(targets)} of 4096 target blocks with full upward/downward passes; "
                          f"{dt:.1f} s solve, {setup:.1f} s LGF/kernel-spectrum setup excluded"}
@@ -285,6 +291,8 @@ def run_ours(a, rank, world, dist):
     NW = 2 * N * 2 * N * (N + 1)
     rows = {}
     for prec, rs in (("fp32", 4), ("fp64", 8)):
+        if prec not in res:
+            continue
         r = res[prec]
         w = r["work"]
         mac_ms = r["stages_ms"]["spectrum_mac"]
@@ -315,11 +323,12 @@ def run_ours(a, rank, world, dist):
                    "l2": "flushed before every timed step (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "rel_err": acc,
-        "fp64_plain": {"value": dof * world / (res["fp64"]["ms_per_step"] / 1e3), "unit": "DoF/s",
-                       "ms_per_step": res["fp64"]["ms_per_step"], "steps": res["fp64"]["steps"],
-                       "stages_ms": res["fp64"]["stages_ms"],
-                       "spectrum_mac_tflops": rows["fp64"]["mac_tflops"],
-                       "spectrum_mac_frac_of_fp64_nominal": (rows["fp64"]["mac_tflops"] or 0) / FP64_NOMINAL_TFLOPS},
+        "fp64_plain": None if "fp64" not in res else {
+            "value": dof * world / (res["fp64"]["ms_per_step"] / 1e3), "unit": "DoF/s",
+            "ms_per_step": res["fp64"]["ms_per_step"], "steps": res["fp64"]["steps"],
+            "stages_ms": res["fp64"]["stages_ms"],
+            "spectrum_mac_tflops": rows["fp64"]["mac_tflops"],
+            "spectrum_mac_frac_of_fp64_nominal": (rows["fp64"]["mac_tflops"] or 0) / FP64_NOMINAL_TFLOPS},
         "roofline": {"bound": "alu", "kernel": "hadamard_kernel<float,2> (spectrum MAC, a3)",
                      "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": (ach / FP32_ALU_PEAK_TFLOPS) if ach else None,
@@ -333,8 +342,9 @@ def run_ours(a, rank, world, dist):
                         "fft_inverse_frac": rows["fp32"]["fft_inv_gbs"] / hbm},
         "stages_ms": res["fp32"]["stages_ms"],
         "cpu_baseline": cpu,
-        "e2e": {"value": dof * world / (e2e_ms_step / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms_step},
+        "e2e": None if e2e_ms_step is None else {
+            "value": dof * world / (e2e_ms_step / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms_step},
         "gpu_launches": res["fp32"]["launches"] * a.steps,
         "clocks": res["fp32"]["clocks"],
     }

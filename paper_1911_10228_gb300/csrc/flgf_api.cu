@@ -166,6 +166,7 @@ struct flgf_blockset {
   int timed_solves = 0;
   bool ev_pending = false;
   int64_t launches = 0;  // kernels enqueued by the last solve
+  bool capturing = false;
 };
 
 // ----------------------------------------------------------------------------
@@ -818,11 +819,19 @@ struct StageScope {
     }
     auto& slot = bs->ev[bs->ev_used++];
     slot.first = s;
-    cudaEventRecord(slot.second.first, bs->ctx->stream);
+    record(slot.second.first);
     end = slot.second.second;
   }
+  // Inside stream capture a plain record only orders work; an external
+  // record node is needed for the event to be timed when the graph runs.
+  void record(cudaEvent_t e) const {
+    if (bs->capturing)
+      cudaEventRecordWithFlags(e, bs->ctx->stream, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, bs->ctx->stream);
+  }
   ~StageScope() {
-    if (end) cudaEventRecord(end, bs->ctx->stream);
+    if (end) record(end);
   }
 };
 
@@ -906,6 +915,8 @@ void collect_times(flgf_blockset* bs) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, bs->ev[i].second.first, bs->ev[i].second.second) == cudaSuccess)
       bs->stage_ms[bs->ev[i].first] += ms;
+    else
+      (void)cudaGetLastError();  // a missing timing must not poison later calls
   }
   bs->timed_solves++;
   bs->ev_pending = false;
@@ -949,7 +960,9 @@ extern "C" int flgf_solve(flgf_blockset* bs) {
       bs->ev_used = 0;
       cudaGraph_t g = nullptr;
       CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      bs->capturing = true;
       e = ctx->prec == FLGF_FP64 ? enqueue_solve<double>(bs) : enqueue_solve<float>(bs);
+      bs->capturing = false;
       cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
       if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);

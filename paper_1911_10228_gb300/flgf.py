@@ -230,8 +230,13 @@ class BlockSet:
         torch.cuda.current_stream(self.ctx.device).wait_stream(self.ctx.stream)
         return out
 
-    def potential_host(self, problem: int = 0, level: int = 0) -> np.ndarray:
-        out = np.empty(self._shape(problem, level), dtype=np.float64 if self.ctx.precision == "fp64" else np.float32)
+    def potential_host(self, problem: int = 0, level: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+        """u into host memory (``out``: e.g. a pinned buffer of the right shape and dtype)."""
+        dt = np.float64 if self.ctx.precision == "fp64" else np.float32
+        if out is None:
+            out = np.empty(self._shape(problem, level), dtype=dt)
+        if out.dtype != dt or tuple(out.shape) != self._shape(problem, level) or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous array of the level's shape and the context dtype")
         self.ctx.check(self.lib.flgf_get_potential(self.handle, problem, level, ctypes.c_void_p(out.ctypes.data),
                                                    FLGF_HOST), "flgf_get_potential")
         return out

@@ -100,14 +100,23 @@ class Problem:
 def plain_gaussians(nblk: int, N: int, n_gauss: int, sigma_rng, inner, seed: int = 0,
                     h0: float = 1.0) -> Problem:
     """nblk^3 blocks of N^3 cells; Gaussians with sigma ~ U(sigma_rng) cells, centres
-    ~ U(inner) cells (lattice units, cell centres at i + 1/2), amplitudes ~ U(-1, 1)."""
+    ~ U(inner) cells (lattice units, cell centres at i + 1/2), amplitudes ~ U(-1, 1).
+
+    The box is dense, so each Gaussian is evaluated as the product of its three
+    1-D factors on the cell-centre axis and then cut into blocks.
+    """
     rng = np.random.default_rng(seed)
     sig = rng.uniform(sigma_rng[0], sigma_rng[1], n_gauss)
     cen = rng.uniform(inner[0], inner[1], (n_gauss, 3))
     amp = rng.uniform(-1.0, 1.0, n_gauss)
     coords = box_coords(nblk)
-    x = cell_centres(coords, N, 1.0)
-    f = truncate(gaussians(x, cen, sig, amp))
+    ax = np.arange(nblk * N) + 0.5
+    dense = np.zeros((nblk * N,) * 3)
+    for c, s, a in zip(cen, sig, amp):
+        e = [np.exp(-(ax - c[d]) ** 2 / (2.0 * s * s)) for d in range(3)]
+        dense += a * (e[0][:, None, None] * e[1][None, :, None] * e[2][None, None, :])
+    f = dense.reshape(nblk, N, nblk, N, nblk, N).transpose(0, 2, 4, 1, 3, 5).reshape(-1, N, N, N)
+    f = truncate(f)
     return Problem(N=N, h0=h0, coords=[coords], f=[f], name=f"gauss{nblk}x{N}")
 
 
