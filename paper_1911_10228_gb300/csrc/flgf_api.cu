@@ -497,7 +497,7 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
   }
   // ---- launch lists ----------------------------------------------------------
   Arena& ar = bs->ar;
-  const int TP[3] = {4, 8, 8};  // tile size in parents
+  const int TP[3] = {4, 4, 8};  // tile size in parents (<= 128 parents: 256 threads, two CTAs per SM)
   for (int l = 0; l < bs->Lmax; ++l) {
     PhaseOff& ph = bs->ph[l];
     std::vector<int> prep_src, prep_dst;
@@ -870,7 +870,7 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
       KRUN(ph.n_prep, launch_copy_blocks<R>(N, fwork, ar.at<int>(ph.prep_src), nodes, ar.at<int>(ph.prep_dst),
                                 ar.at<uint8_t>(ph.prep_zero), ph.n_prep, s));
       for (int k = 1; k <= maxtop; ++k)
-        KRUN(ph.n_ant[k], launch_anterp<R>(N, c->d_J1, ar.at<int>(ph.ant_par[k]), ar.at<int>(ph.ant_ch[k]), ph.n_ant[k], nodes, s));
+        KRUN(ph.n_ant[k], launch_anterp<R>(N, c->nI, c->d_J1, ar.at<int>(ph.ant_par[k]), ar.at<int>(ph.ant_ch[k]), ph.n_ant[k], nodes, s));
     }
     {
       StageScope sc(bs, 2);
@@ -890,7 +890,7 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
     {
       StageScope sc(bs, 5);
       for (int k = maxtop - 1; k >= 0; --k)
-        KRUN(ph.n_itp[k], launch_interp_add<R>(N, c->d_J1, ar.at<int>(ph.itp_ch[k]), ar.at<int>(ph.itp_par[k]),
+        KRUN(ph.n_itp[k], launch_interp_add<R>(N, c->nI, c->d_J1, ar.at<int>(ph.itp_ch[k]), ar.at<int>(ph.itp_par[k]),
                                  ar.at<int>(ph.itp_cpos[k]), ph.n_itp[k], unodes, s));
     }
     {

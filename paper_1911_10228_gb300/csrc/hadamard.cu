@@ -15,29 +15,35 @@
 // CTA = (tile of parents) x (one chunk of T frequencies).  Shared memory holds
 // the chunk of the 343 kernel spectra of this octree level and the chunk of
 // every source block in the tile's region (tile grown by one parent on each
-// side, clipped to the level's bounding box; absent blocks are zero).
-// Near offsets |d|_inf <= 1 are zeroed in shared memory on levels that
-// exclude the near field, and e = 0 is skipped there entirely.
+// side, clipped to the level's bounding box; absent blocks are zero).  The
+// region is stored parity-major, [freq group][child position b][parent cell
+// q][TT], so the 32 threads of a warp (consecutive parents) read 32
+// consecutive 16-byte vectors: no bank conflicts.  Near offsets |d|_inf <= 1
+// are zeroed in shared memory on levels that exclude the near field, and
+// e = 0 is skipped there entirely.  Complex multiply-adds are written as four
+// fused multiply-adds.
 #include "common.cuh"
 #include "internal.h"
 
 namespace flgf {
 
 template <typename R, int TT>
-__global__ void __launch_bounds__(512) hadamard_kernel(const HadTile* __restrict__ tiles, const int* __restrict__ src_ids,
-                                                       const int* __restrict__ tgt_ids, const cplx<R>* __restrict__ spec,
-                                                       cplx<R>* __restrict__ acc, int spec_blocks,
-                                                       const cplx<R>* __restrict__ kspec, size_t kstride) {
+__global__ void __launch_bounds__(256, 2) hadamard_kernel(const HadTile* __restrict__ tiles, const int* __restrict__ src_ids,
+                                                          const int* __restrict__ tgt_ids, const cplx<R>* __restrict__ spec,
+                                                          cplx<R>* __restrict__ acc, int spec_blocks,
+                                                          const cplx<R>* __restrict__ kspec, size_t kstride) {
   constexpr int T = ChunkT<R>::value;
+  constexpr int NG = T / TT;  // frequency groups per chunk
+  static_assert(TT * sizeof(cplx<R>) == 16, "one 16-byte vector per (group, cell)");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<R>* Ks = reinterpret_cast<cplx<R>*>(smem_raw);  // [343][T]
-  cplx<R>* Fs = Ks + kNOff * T;                        // [cells][T]
+  int4* Fs = reinterpret_cast<int4*>(Ks + kNOff * T);   // [NG][8][NQ] 16-byte vectors
   const HadTile tl = tiles[blockIdx.x];
   const int chunk = blockIdx.y;
   const int nthreads = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
 
-  // kernel spectra chunk (32 bytes per offset) -- copied as 16-byte vectors
+  // kernel spectra chunk (32 bytes per offset)
   {
     const int4* ksrc = reinterpret_cast<const int4*>(kspec + (size_t)tl.level * kstride + (size_t)chunk * kNOff * T);
     int4* kdst = reinterpret_cast<int4*>(Ks);
@@ -49,17 +55,20 @@ __global__ void __launch_bounds__(512) hadamard_kernel(const HadTile* __restrict
       kdst[i] = (tl.excl_near && near) ? zero4 : ksrc[i];
     }
   }
-  // source region chunk
-  const int C1 = 2 * tl.Rg[1], C2 = 2 * tl.Rg[2];
-  const int ncell = 2 * tl.Rg[0] * C1 * C2;
+  // source region chunk, natural cell order in HBM -> parity-major in shared memory
+  const int R1 = tl.Rg[1], R2 = tl.Rg[2];
+  const int NQ = tl.Rg[0] * R1 * R2;
+  const int C1 = 2 * R1, C2 = 2 * R2;
   {
-    int4* fdst = reinterpret_cast<int4*>(Fs);
     const int4* fsrc = reinterpret_cast<const int4*>(spec + (size_t)chunk * spec_blocks * T);
     const int4 zero4 = make_int4(0, 0, 0, 0);
-    for (int i = tid; i < ncell * 2; i += nthreads) {
-      const int cell = i >> 1;
+    for (int i = tid; i < 8 * NQ * NG; i += nthreads) {
+      const int cell = i / NG, g = i % NG;
+      const int x = cell / (C1 * C2), y = (cell / C2) % C1, z = cell % C2;
+      const int b = ((x & 1) << 2) | ((y & 1) << 1) | (z & 1);
+      const int q = ((x >> 1) * R1 + (y >> 1)) * R2 + (z >> 1);
       const int sid = src_ids[tl.src_off + cell];
-      fdst[i] = sid >= 0 ? fsrc[(size_t)sid * 2 + (i & 1)] : zero4;
+      Fs[(g * 8 + b) * NQ + q] = sid >= 0 ? fsrc[(size_t)sid * NG + g] : zero4;
     }
   }
   __syncthreads();
@@ -67,10 +76,12 @@ __global__ void __launch_bounds__(512) hadamard_kernel(const HadTile* __restrict
   const int np = tl.P[0] * tl.P[1] * tl.P[2];
   const int pl = threadIdx.x;
   if (pl >= np) return;
-  const int f0 = threadIdx.y * TT;
+  const int g = threadIdx.y;
+  const int f0 = g * TT;
   const int pq[3] = {pl / (tl.P[1] * tl.P[2]), (pl / tl.P[2]) % tl.P[1], pl % tl.P[2]};
   // parent position inside the region
   const int q0 = tl.p0[0] + pq[0] - tl.r0[0], q1 = tl.p0[1] + pq[1] - tl.r0[1], q2 = tl.p0[2] + pq[2] - tl.r0[2];
+  const cplx<R>* Fg = reinterpret_cast<const cplx<R>*>(Fs + (size_t)g * 8 * NQ);
 
   R ar[8][TT], ai[8][TT];
 #pragma unroll
@@ -82,8 +93,8 @@ __global__ void __launch_bounds__(512) hadamard_kernel(const HadTile* __restrict
     const int e0 = e / 9 - 1, e1 = (e / 3) % 3 - 1, e2 = e % 3 - 1;
     if (tl.excl_near && e == 13) continue;
     const int n0 = q0 + e0, n1 = q1 + e1, n2 = q2 + e2;
-    if (n0 < 0 || n0 >= tl.Rg[0] || n1 < 0 || n1 >= tl.Rg[1] || n2 < 0 || n2 >= tl.Rg[2]) continue;
-    const cplx<R>* fb = Fs + ((size_t)((2 * n0) * C1 + 2 * n1) * C2 + 2 * n2) * T + f0;
+    if (n0 < 0 || n0 >= tl.Rg[0] || n1 < 0 || n1 >= R1 || n2 < 0 || n2 >= R2) continue;
+    const cplx<R>* fb = Fg + (size_t)((n0 * R1 + n1) * R2 + n2) * TT;
     // offset index of d = a - b - 2e is kbase + (a0-b0)*49 + (a1-b1)*7 + (a2-b2)
     const cplx<R>* kb = Ks + (size_t)off_index(-2 * e0, -2 * e1, -2 * e2) * T + f0;
 #pragma unroll
@@ -92,7 +103,7 @@ __global__ void __launch_bounds__(512) hadamard_kernel(const HadTile* __restrict
       R fr[TT], fi[TT];
 #pragma unroll
       for (int t = 0; t < TT; ++t) {
-        const cplx<R> v = fb[((b0 * C1 + b1) * C2 + b2) * T + t];
+        const cplx<R> v = fb[(size_t)b * NQ * TT + t];
         fr[t] = v.re; fi[t] = v.im;
       }
 #pragma unroll
@@ -102,8 +113,10 @@ __global__ void __launch_bounds__(512) hadamard_kernel(const HadTile* __restrict
 #pragma unroll
         for (int t = 0; t < TT; ++t) {
           const cplx<R> k = kb[dk * T + t];
-          ar[a][t] += k.re * fr[t] - k.im * fi[t];
-          ai[a][t] += k.re * fi[t] + k.im * fr[t];
+          ar[a][t] = fma(k.re, fr[t], ar[a][t]);
+          ar[a][t] = fma(-k.im, fi[t], ar[a][t]);
+          ai[a][t] = fma(k.re, fi[t], ai[a][t]);
+          ai[a][t] = fma(k.im, fr[t], ai[a][t]);
         }
       }
     }
@@ -131,7 +144,7 @@ cudaError_t launch_hadamard(int N, const HadTile* tiles, int ntiles, int max_par
   constexpr int TT = (sizeof(R) == 4) ? 2 : 1;
   const int ng = T / TT;
   int bx = ((max_parents + 31) / 32) * 32;
-  if (bx * ng > 512) return cudaErrorInvalidConfiguration;
+  if (bx * ng > 256) return cudaErrorInvalidConfiguration;
   const size_t sm = sizeof(cplx<R>) * T * ((size_t)kNOff + max_region_cells);
   if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(hadamard_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -56,10 +56,10 @@ cudaError_t launch_hadamard(int N, const HadTile* tiles, int ntiles, int max_par
 // ---- a1/a5 and multi-resolution stencils (stencil.cu) ----------------------
 // J1: dense 1-D Lagrange matrix [2N][N] (row = child node of the two children, column = parent node).
 template <typename R>
-cudaError_t launch_anterp(int N, const double* J1, const int* parents, const int* children /*[n][8]*/, int n,
-                          R* nodes, cudaStream_t s);
+cudaError_t launch_anterp(int N, int nI, const double* J1, const int* parents, const int* children /*[n][8]*/,
+                          int n, R* nodes, cudaStream_t s);
 template <typename R>
-cudaError_t launch_interp_add(int N, const double* J1, const int* childs, const int* parents, const int* cpos,
+cudaError_t launch_interp_add(int N, int nI, const double* J1, const int* childs, const int* parents, const int* cpos,
                               int n, R* unodes, cudaStream_t s);
 // dst[dst_ids[i]] = src[src_ids[i]] * (mask? mask[i] : 1)
 template <typename R>

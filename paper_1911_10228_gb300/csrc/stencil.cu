@@ -14,93 +14,140 @@
 
 namespace flgf {
 
-template <typename R>
-__global__ void anterp_kernel(int N, const double* __restrict__ J1, const int* __restrict__ parents,
-                              const int* __restrict__ children, R* __restrict__ nodes) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N3 = N * N * N;
-  R* J = reinterpret_cast<R*>(smem_raw);  // [2N][N]
-  R* A = J + 2 * N * N;
-  R* B = A + N3;
-  R* Pacc = B + N3;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < 2 * N * N; i += nt) J[i] = (R)J1[i];
-  for (int i = tid; i < N3; i += nt) Pacc[i] = R(0);
-  const int parent = parents[blockIdx.x];
+// First parent node of the n_I-point Lagrange window of child node j
+// (0..2N-1) for cell-centred nodes (child j at j + 1/2, parent p at 2p + 1, in
+// child spacings): centred on the point, moved inwards at the faces.
+template <int N, int NI>
+__host__ __device__ constexpr int band_start(int j) {
+  const int lo = j == 0 ? -1 : (j - 1) / 2;      // parent node just left of the point
+  const int near = (j % 2 == 0) ? j / 2 : (j - 1) / 2;  // nearest parent node
+  const int s = (NI % 2 == 0) ? lo - (NI / 2 - 1) : near - NI / 2;
+  return s < 0 ? 0 : (s > N - NI ? N - NI : s);
+}
+
+// Shared-memory block with padded rows: element (i, j, k) at (i*N + j)*(N+1) + k.
+template <int N>
+__device__ __forceinline__ int pidx(int i, int j, int k) { return (i * N + j) * (N + 1) + k; }
+
+// One 1-D pass of interpolation (child position C along the axis) on a line
+// held in registers: out[r] = sum_m W[C N + r][m] in[band_start(C N + r) + m].
+template <typename R, int N, int NI, int C>
+__device__ __forceinline__ void line_interp(const R* in, R* out, const R* W) {
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const int j = C * N + r;
+    R s = R(0);
+#pragma unroll
+    for (int m = 0; m < NI; ++m) s = fma(W[j * NI + m], in[band_start<N, NI>(j) + m], s);
+    out[r] = s;
+  }
+}
+// Its adjoint (anterpolation): out[q] += sum_r J[C N + r][q] in[r].
+template <typename R, int N, int NI, int C>
+__device__ __forceinline__ void line_anterp(const R* in, R* out, const R* W) {
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const int j = C * N + r;
+#pragma unroll
+    for (int m = 0; m < NI; ++m) {
+      const int q = band_start<N, NI>(j) + m;
+      out[q] = fma(W[j * NI + m], in[r], out[q]);
+    }
+  }
+}
+
+// Load the banded weights W[j][m] = J1[j][band_start(j) + m] into shared memory.
+template <typename R, int N, int NI>
+__device__ __forceinline__ void load_band(const double* __restrict__ J1, R* W) {
+  for (int i = threadIdx.x; i < 2 * N * NI; i += blockDim.x) {
+    const int j = i / NI, m = i % NI;
+    int s = (NI % 2 == 0) ? (j == 0 ? -1 : (j - 1) / 2) - (NI / 2 - 1) : ((j % 2 == 0) ? j / 2 : (j - 1) / 2) - NI / 2;
+    s = s < 0 ? 0 : (s > N - NI ? N - NI : s);
+    W[i] = (R)J1[j * N + s + m];
+  }
+}
+
+// a1: parent += sum over existing children of (R_c0 x R_c1 x R_c2) child.
+// One thread per line; N^2 threads.  Axis-2 lines are contiguous (padded rows
+// keep them conflict-free), axis-1 and axis-0 lines are strided.
+template <typename R, int N, int NI>
+__global__ void __launch_bounds__(N * N) anterp_kernel(const double* __restrict__ J1, const int* __restrict__ parents,
+                                                       const int* __restrict__ children, R* __restrict__ nodes) {
+  constexpr int N3 = N * N * N, PS = N * N * (N + 1);
+  __shared__ R W[2 * N * NI];
+  __shared__ R A[PS];  // each thread transforms whole lines in place
+  load_band<R, N, NI>(J1, W);
+  const int t = threadIdx.x, u = t / N, v = t % N;
+  R acc[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) acc[q] = R(0);
   for (int c = 0; c < 8; ++c) {
     const int cid = children[blockIdx.x * 8 + c];
     if (cid < 0) continue;
     const int c0 = c >> 2, c1 = (c >> 1) & 1, c2 = c & 1;
     __syncthreads();
     const R* src = nodes + (size_t)cid * N3;
-    for (int i = tid; i < N3; i += nt) A[i] = src[i];
+    for (int i = t; i < N3; i += blockDim.x) A[pidx<N>(i / (N * N), (i / N) % N, i % N)] = src[i];
     __syncthreads();
-    // axis 2: B[i][j][q] = sum_r J[c2 N + r][q] A[i][j][r]
-    for (int o = tid; o < N3; o += nt) {
-      const int q = o % N, ij = o / N;
-      R s = 0;
-      for (int r = 0; r < N; ++r) s += J[(c2 * N + r) * N + q] * A[ij * N + r];
-      B[o] = s;
-    }
+    R in[N], out[N];
+    // axis 2: line (u, v) = A[u][v][:]
+#pragma unroll
+    for (int k = 0; k < N; ++k) { in[k] = A[pidx<N>(u, v, k)]; out[k] = R(0); }
+    if (c2) line_anterp<R, N, NI, 1>(in, out, W); else line_anterp<R, N, NI, 0>(in, out, W);
+#pragma unroll
+    for (int k = 0; k < N; ++k) A[pidx<N>(u, v, k)] = out[k];
     __syncthreads();
-    // axis 1: A[i][q][k] = sum_r J[c1 N + r][q] B[i][r][k]
-    for (int o = tid; o < N3; o += nt) {
-      const int k = o % N, q = (o / N) % N, i = o / (N * N);
-      R s = 0;
-      for (int r = 0; r < N; ++r) s += J[(c1 * N + r) * N + q] * B[(i * N + r) * N + k];
-      A[o] = s;
-    }
+    // axis 1: line (u, v) = A[u][:][v]
+#pragma unroll
+    for (int j = 0; j < N; ++j) { in[j] = A[pidx<N>(u, j, v)]; out[j] = R(0); }
+    if (c1) line_anterp<R, N, NI, 1>(in, out, W); else line_anterp<R, N, NI, 0>(in, out, W);
+#pragma unroll
+    for (int j = 0; j < N; ++j) A[pidx<N>(u, j, v)] = out[j];
     __syncthreads();
-    // axis 0: Pacc[q][j][k] += sum_r J[c0 N + r][q] A[r][j][k]
-    for (int o = tid; o < N3; o += nt) {
-      const int jk = o % (N * N), q = o / (N * N);
-      R s = 0;
-      for (int r = 0; r < N; ++r) s += J[(c0 * N + r) * N + q] * A[r * N * N + jk];
-      Pacc[o] += s;
-    }
+    // axis 0: line (u, v) = A[:][u][v], accumulated in registers
+#pragma unroll
+    for (int i = 0; i < N; ++i) in[i] = A[pidx<N>(i, u, v)];
+    if (c0) line_anterp<R, N, NI, 1>(in, acc, W); else line_anterp<R, N, NI, 0>(in, acc, W);
   }
-  __syncthreads();
-  R* dst = nodes + (size_t)parent * N3;
-  for (int i = tid; i < N3; i += nt) dst[i] = Pacc[i];
+  R* dst = nodes + (size_t)parents[blockIdx.x] * N3;
+#pragma unroll
+  for (int i = 0; i < N; ++i) dst[(i * N + u) * N + v] = acc[i];
 }
 
-template <typename R>
-__global__ void interp_add_kernel(int N, const double* __restrict__ J1, const int* __restrict__ childs,
-                                  const int* __restrict__ parents, const int* __restrict__ cpos,
-                                  R* __restrict__ unodes) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N3 = N * N * N;
-  R* J = reinterpret_cast<R*>(smem_raw);
-  R* A = J + 2 * N * N;
-  R* B = A + N3;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < 2 * N * N; i += nt) J[i] = (R)J1[i];
-  const int child = childs[blockIdx.x], parent = parents[blockIdx.x], c = cpos[blockIdx.x];
+// a5: child += (J_c0 x J_c1 x J_c2) parent.
+template <typename R, int N, int NI>
+__global__ void __launch_bounds__(N * N) interp_add_kernel(const double* __restrict__ J1, const int* __restrict__ childs,
+                                                           const int* __restrict__ parents, const int* __restrict__ cpos,
+                                                           R* __restrict__ unodes) {
+  constexpr int N3 = N * N * N, PS = N * N * (N + 1);
+  __shared__ R W[2 * N * NI];
+  __shared__ R A[PS];  // each thread transforms whole lines in place
+  load_band<R, N, NI>(J1, W);
+  const int t = threadIdx.x, u = t / N, v = t % N;
+  const int c = cpos[blockIdx.x];
   const int c0 = c >> 2, c1 = (c >> 1) & 1, c2 = c & 1;
-  const R* src = unodes + (size_t)parent * N3;
-  for (int i = tid; i < N3; i += nt) A[i] = src[i];
+  const R* src = unodes + (size_t)parents[blockIdx.x] * N3;
+  for (int i = t; i < N3; i += blockDim.x) A[pidx<N>(i / (N * N), (i / N) % N, i % N)] = src[i];
   __syncthreads();
-  for (int o = tid; o < N3; o += nt) {  // axis 2
-    const int r = o % N, ij = o / N;
-    R s = 0;
-    for (int q = 0; q < N; ++q) s += J[(c2 * N + r) * N + q] * A[ij * N + q];
-    B[o] = s;
-  }
+  R in[N], out[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) in[k] = A[pidx<N>(u, v, k)];
+  if (c2) line_interp<R, N, NI, 1>(in, out, W); else line_interp<R, N, NI, 0>(in, out, W);
+#pragma unroll
+  for (int k = 0; k < N; ++k) A[pidx<N>(u, v, k)] = out[k];
   __syncthreads();
-  for (int o = tid; o < N3; o += nt) {  // axis 1
-    const int k = o % N, r = (o / N) % N, i = o / (N * N);
-    R s = 0;
-    for (int q = 0; q < N; ++q) s += J[(c1 * N + r) * N + q] * B[(i * N + q) * N + k];
-    A[o] = s;
-  }
+#pragma unroll
+  for (int j = 0; j < N; ++j) in[j] = A[pidx<N>(u, j, v)];
+  if (c1) line_interp<R, N, NI, 1>(in, out, W); else line_interp<R, N, NI, 0>(in, out, W);
+#pragma unroll
+  for (int j = 0; j < N; ++j) A[pidx<N>(u, j, v)] = out[j];
   __syncthreads();
-  R* dst = unodes + (size_t)child * N3;
-  for (int o = tid; o < N3; o += nt) {  // axis 0
-    const int jk = o % (N * N), r = o / (N * N);
-    R s = 0;
-    for (int q = 0; q < N; ++q) s += J[(c0 * N + r) * N + q] * A[q * N * N + jk];
-    dst[o] += s;
-  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) in[i] = A[pidx<N>(i, u, v)];
+  if (c0) line_interp<R, N, NI, 1>(in, out, W); else line_interp<R, N, NI, 0>(in, out, W);
+  R* dst = unodes + (size_t)childs[blockIdx.x] * N3;
+#pragma unroll
+  for (int i = 0; i < N; ++i) dst[(i * N + u) * N + v] += out[i];
 }
 
 template <typename R>
@@ -256,27 +303,59 @@ static cudaError_t set_smem(Kern k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename R>
-cudaError_t launch_anterp(int N, const double* J1, const int* parents, const int* children, int n, R* nodes,
-                          cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const size_t sm = sizeof(R) * (2 * N * N + 3 * N * N * N);
-  cudaError_t e = set_smem(anterp_kernel<R>, sm);
-  if (e != cudaSuccess) return e;
-  anterp_kernel<R><<<n, threads_for(N), sm, s>>>(N, J1, parents, children, nodes);
+template <typename R, int N, int NI>
+static cudaError_t anterp_n(const double* J1, const int* parents, const int* children, int n, R* nodes, cudaStream_t s) {
+  anterp_kernel<R, N, NI><<<n, N * N, 0, s>>>(J1, parents, children, nodes);
+  return cudaGetLastError();
+}
+template <typename R, int N, int NI>
+static cudaError_t interp_n(const double* J1, const int* childs, const int* parents, const int* cpos, int n, R* unodes,
+                            cudaStream_t s) {
+  interp_add_kernel<R, N, NI><<<n, N * N, 0, s>>>(J1, childs, parents, cpos, unodes);
   return cudaGetLastError();
 }
 
+// Dispatch over the supported (N, n_I): N in {8, 16}, 2 <= n_I <= min(N, 10).
+#define FLGF_NI_CASES(N, F, ...)            \
+  switch (nI) {                             \
+    case 2: return F<R, N, 2>(__VA_ARGS__);  \
+    case 3: return F<R, N, 3>(__VA_ARGS__);  \
+    case 4: return F<R, N, 4>(__VA_ARGS__);  \
+    case 5: return F<R, N, 5>(__VA_ARGS__);  \
+    case 6: return F<R, N, 6>(__VA_ARGS__);  \
+    case 7: return F<R, N, 7>(__VA_ARGS__);  \
+    case 8: return F<R, N, 8>(__VA_ARGS__);  \
+    default: break;                         \
+  }
+
 template <typename R>
-cudaError_t launch_interp_add(int N, const double* J1, const int* childs, const int* parents, const int* cpos,
+cudaError_t launch_anterp(int N, int nI, const double* J1, const int* parents, const int* children, int n, R* nodes,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (N == 16) {
+    FLGF_NI_CASES(16, anterp_n, J1, parents, children, n, nodes, s)
+    if (nI == 9) return anterp_n<R, 16, 9>(J1, parents, children, n, nodes, s);
+    if (nI == 10) return anterp_n<R, 16, 10>(J1, parents, children, n, nodes, s);
+  } else if (N == 8) {
+    FLGF_NI_CASES(8, anterp_n, J1, parents, children, n, nodes, s)
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R>
+cudaError_t launch_interp_add(int N, int nI, const double* J1, const int* childs, const int* parents, const int* cpos,
                               int n, R* unodes, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const size_t sm = sizeof(R) * (2 * N * N + 2 * N * N * N);
-  cudaError_t e = set_smem(interp_add_kernel<R>, sm);
-  if (e != cudaSuccess) return e;
-  interp_add_kernel<R><<<n, threads_for(N), sm, s>>>(N, J1, childs, parents, cpos, unodes);
-  return cudaGetLastError();
+  if (N == 16) {
+    FLGF_NI_CASES(16, interp_n, J1, childs, parents, cpos, n, unodes, s)
+    if (nI == 9) return interp_n<R, 16, 9>(J1, childs, parents, cpos, n, unodes, s);
+    if (nI == 10) return interp_n<R, 16, 10>(J1, childs, parents, cpos, n, unodes, s);
+  } else if (N == 8) {
+    FLGF_NI_CASES(8, interp_n, J1, childs, parents, cpos, n, unodes, s)
+  }
+  return cudaErrorInvalidValue;
 }
+#undef FLGF_NI_CASES
 
 template <typename R>
 cudaError_t launch_copy_blocks(int N, const R* src, const int* src_ids, R* dst, const int* dst_ids,
@@ -315,8 +394,8 @@ cudaError_t launch_laplacian(int N, const R* u, const int* nbr6, int n, double i
 }
 
 #define FLGF_INST(R)                                                                                            \
-  template cudaError_t launch_anterp<R>(int, const double*, const int*, const int*, int, R*, cudaStream_t);      \
-  template cudaError_t launch_interp_add<R>(int, const double*, const int*, const int*, const int*, int, R*,    \
+  template cudaError_t launch_anterp<R>(int, int, const double*, const int*, const int*, int, R*, cudaStream_t); \
+  template cudaError_t launch_interp_add<R>(int, int, const double*, const int*, const int*, const int*, int, R*, \
                                             cudaStream_t);                                                      \
   template cudaError_t launch_copy_blocks<R>(int, const R*, const int*, R*, const int*, const uint8_t*, int,    \
                                              cudaStream_t);                                                     \
