@@ -99,7 +99,9 @@ int flgf_lgf_eval(flgf_ctx* ctx, int n_pts, const int32_t* pts, double* out);
 /* Kernel spectrum of octree level k and block offset d = (d0, d1, d2) in
  * [-3, 3]^3, in natural order [k0 < 2N][k1 < 2N][k2 <= N] as interleaved
  * (re, im) doubles written to host memory out[2 * 4N^2(N+1)].  In FP32
- * contexts the stored single-precision values are widened.  Synchronises. */
+ * contexts the stored single-precision values are widened.  Octree levels
+ * k >= 1 never use the near offsets |d|_inf <= 1 (the near field belongs to
+ * the finest level) and store them as zero.  Synchronises. */
 int flgf_kernel_spectrum(flgf_ctx* ctx, int k, int d0, int d1, int d2, double* out);
 
 /* Create a block set holding n_problems independent problems (1 for a plain

@@ -306,9 +306,11 @@ __global__ void __launch_bounds__(N * N) fft_kernel_half(const double* __restric
   }
 }
 
+// Octree levels >= 1 never use the near offsets |d|_inf <= 1 (the near field
+// belongs to the finest level), so their spectra are stored as zero.
 template <typename R>
 __global__ void kernel_combine(const cplx<double>* __restrict__ lo, const cplx<double>* __restrict__ hi, int N,
-                               cplx<R>* __restrict__ kspec) {
+                               int zero_near, cplx<R>* __restrict__ kspec) {
   const int P = 2 * N, NX = N + 1, NW = P * P * NX;
   constexpr int T = ChunkT<R>::value;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -317,6 +319,12 @@ __global__ void kernel_combine(const cplx<double>* __restrict__ lo, const cplx<d
   const int k0 = w / (P * NX);
   const cplx<double> a = lo[idx], b = hi[idx];
   const double sg = (k0 & 1) ? -1.0 : 1.0;
+  const int dd0 = d / 49 - 3, dd1 = (d / 7) % 7 - 3, dd2 = d % 7 - 3;
+  const bool near = dd0 >= -1 && dd0 <= 1 && dd1 >= -1 && dd1 <= 1 && dd2 >= -1 && dd2 <= 1;
+  if (zero_near && near) {
+    kspec[((size_t)(w / T) * kNOff + d) * T + (w % T)] = cplx<R>{R(0), R(0)};
+    return;
+  }
   // layout [chunk][343][T]
   kspec[((size_t)(w / T) * kNOff + d) * T + (w % T)] = cplx<R>{(R)(a.re + sg * b.re), (R)(a.im + sg * b.im)};
 }
@@ -365,7 +373,7 @@ cudaError_t launch_fft_inverse(int N, const void* acc, int spec_blocks, const in
 }
 
 template <typename R>
-cudaError_t launch_kernel_spectra(int N, const double* karr, void* kspec_level, double* tmp, cudaStream_t s) {
+cudaError_t launch_kernel_spectra(int N, const double* karr, void* kspec_level, double* tmp, int zero_near, cudaStream_t s) {
   const int P = 2 * N, NW = P * P * (N + 1);
   cplx<double>* lo = reinterpret_cast<cplx<double>*>(tmp);
   cplx<double>* hi = lo + (size_t)kNOff * NW;
@@ -383,7 +391,8 @@ cudaError_t launch_kernel_spectra(int N, const double* karr, void* kspec_level, 
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t total = (size_t)NW * kNOff;
-  kernel_combine<R><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(lo, hi, N, reinterpret_cast<cplx<R>*>(kspec_level));
+  kernel_combine<R><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(lo, hi, N, zero_near,
+                                                                     reinterpret_cast<cplx<R>*>(kspec_level));
   return cudaGetLastError();
 }
 
@@ -391,7 +400,7 @@ template cudaError_t launch_fft_forward<float>(int, const float*, const int*, co
 template cudaError_t launch_fft_forward<double>(int, const double*, const int*, const int*, int, void*, int, cudaStream_t);
 template cudaError_t launch_fft_inverse<float>(int, const void*, int, const int*, const int*, const double*, int, float*, cudaStream_t);
 template cudaError_t launch_fft_inverse<double>(int, const void*, int, const int*, const int*, const double*, int, double*, cudaStream_t);
-template cudaError_t launch_kernel_spectra<float>(int, const double*, void*, double*, cudaStream_t);
-template cudaError_t launch_kernel_spectra<double>(int, const double*, void*, double*, cudaStream_t);
+template cudaError_t launch_kernel_spectra<float>(int, const double*, void*, double*, int, cudaStream_t);
+template cudaError_t launch_kernel_spectra<double>(int, const double*, void*, double*, int, cudaStream_t);
 
 }  // namespace flgf

@@ -129,7 +129,7 @@ struct PhaseOff {  // arena offsets and counts of one phase's launch lists
   int n_prep = 0; size_t prep_src = 0, prep_dst = 0, prep_zero = 0;
   std::vector<int> n_ant; std::vector<size_t> ant_par, ant_ch;
   int n_fwd = 0; size_t fwd_gid = 0, fwd_sid = 0;
-  int n_tiles = 0, max_par = 0, max_cells = 0; size_t tiles = 0, src_ids = 0, tgt_ids = 0;
+  int n_tiles = 0, n_work = 0, max_cells_cpc = 0; size_t tiles = 0, work = 0, src_ids = 0, tgt_ids = 0;
   int n_inv = 0; size_t inv_sid = 0, inv_gid = 0, inv_scale = 0;
   std::vector<int> n_itp; std::vector<size_t> itp_ch, itp_par, itp_cpos;
   int n_sel = 0; size_t sel_src = 0, sel_dst = 0;
@@ -248,9 +248,9 @@ extern "C" int flgf_create(flgf_ctx** out, const flgf_opts* o) {
     STEP(launch_kernel_arrays(ctx->d_table, R, (double)R, (double)ctx->RA, N, k, karr, ctx->stream));
     void* lvl = (char*)ctx->d_kspec + csz * ctx->kstride * k;
     if (ctx->prec == FLGF_FP64) {
-      STEP(launch_kernel_spectra<double>(N, karr, lvl, tmp, ctx->stream));
+      STEP(launch_kernel_spectra<double>(N, karr, lvl, tmp, k >= 1 ? 1 : 0, ctx->stream));
     } else {
-      STEP(launch_kernel_spectra<float>(N, karr, lvl, tmp, ctx->stream));
+      STEP(launch_kernel_spectra<float>(N, karr, lvl, tmp, k >= 1 ? 1 : 0, ctx->stream));
     }
   }
   STEP(cudaStreamSynchronize(ctx->stream));
@@ -510,7 +510,9 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     std::vector<int> fwd_gid, fwd_sid, inv_sid, inv_gid;
     std::vector<double> inv_scale;
     std::vector<HadTile> tiles;
+    std::vector<HadWork> work;
     std::vector<int> src_ids, tgt_ids;
+    const int nchunk = ctx->prec == FLGF_FP64 ? nchunks<double>(N) : nchunks<float>(N);
     for (const auto& in : bs->inst) {
       if (in.l != l) continue;
       const LevelInfo& L = bs->prob[in.p].lev[l];
@@ -586,12 +588,16 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
                     any |= need;
                   }
               if (!any) continue;
-              std::vector<int> sg;
+              // source slots in parity-major order: slot = b * NQ + q
+              const int NQ = tl.Rg[0] * tl.Rg[1] * tl.Rg[2];
+              std::vector<int> sg(8 * NQ, -1);
               for (int x = 0; x < 2 * tl.Rg[0]; ++x)
                 for (int y = 0; y < 2 * tl.Rg[1]; ++y)
                   for (int z = 0; z < 2 * tl.Rg[2]; ++z) {
                     const int i = lookup(2 * tl.r0[0] + x, 2 * tl.r0[1] + y, 2 * tl.r0[2] + z);
-                    sg.push_back(i >= 0 && in.is_src[k][i] ? in.gid0[k] + i - ph.gid_begin : -1);
+                    const int b = ((x & 1) << 2) | ((y & 1) << 1) | (z & 1);
+                    const int qq = ((x >> 1) * tl.Rg[1] + (y >> 1)) * tl.Rg[2] + (z >> 1);
+                    sg[b * NQ + qq] = i >= 0 && in.is_src[k][i] ? in.gid0[k] + i - ph.gid_begin : -1;
                   }
               // count interacting (target, source) pairs for the work accounting
               for (int x = 0; x < 2 * tl.P[0]; ++x)
@@ -602,7 +608,9 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
                     for (int sx = 0; sx < 2 * tl.Rg[0]; ++sx)
                       for (int sy = 0; sy < 2 * tl.Rg[1]; ++sy)
                         for (int sz = 0; sz < 2 * tl.Rg[2]; ++sz) {
-                          if (sg[(sx * 2 * tl.Rg[1] + sy) * 2 * tl.Rg[2] + sz] < 0) continue;
+                          const int b = ((sx & 1) << 2) | ((sy & 1) << 1) | (sz & 1);
+                          const int qq = ((sx >> 1) * tl.Rg[1] + (sy >> 1)) * tl.Rg[2] + (sz >> 1);
+                          if (sg[b * NQ + qq] < 0) continue;
                           const int sc[3] = {2 * tl.r0[0] + sx, 2 * tl.r0[1] + sy, 2 * tl.r0[2] + sz};
                           bool inlist = true, near = true;
                           for (int a = 0; a < 3; ++a) {
@@ -612,12 +620,21 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
                           if (inlist && !(excl && near)) bs->pairs++;
                         }
                   }
+              // threads: (parent slot, frequency group, chunk); small tiles take
+              // several chunks per CTA, bounded by shared memory (~100 KB)
+              const int np = tl.P[0] * tl.P[1] * tl.P[2];
+              tl.pslots = 1;
+              while (tl.pslots < np) tl.pslots <<= 1;
+              int cpc = kHadThreads / (tl.pslots * 2);
+              while (cpc > 1 && 8 * NQ * cpc > 3200) cpc >>= 1;
+              tl.cpc = cpc;
+              ph.max_cells_cpc = std::max(ph.max_cells_cpc, 8 * NQ * cpc);
+              for (int c0 = 0; c0 < nchunk; c0 += cpc)
+                work.push_back(HadWork{(int)tiles.size(), c0, std::min(cpc, nchunk - c0)});
               tl.tgt_off = (int)tgt_ids.size();
               tgt_ids.insert(tgt_ids.end(), tg.begin(), tg.end());
               tl.src_off = (int)src_ids.size();
               src_ids.insert(src_ids.end(), sg.begin(), sg.end());
-              ph.max_par = std::max(ph.max_par, tl.P[0] * tl.P[1] * tl.P[2]);
-              ph.max_cells = std::max(ph.max_cells, 8 * tl.Rg[0] * tl.Rg[1] * tl.Rg[2]);
               tiles.push_back(tl);
             }
       }
@@ -650,6 +667,8 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     ph.fwd_sid = ar.add(fwd_sid);
     ph.n_tiles = (int)tiles.size();
     ph.tiles = ar.add(tiles);
+    ph.n_work = (int)work.size();
+    ph.work = ar.add(work);
     ph.src_ids = ar.add(src_ids);
     ph.tgt_ids = ar.add(tgt_ids);
     ph.n_inv = (int)inv_gid.size();
@@ -879,8 +898,9 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
     }
     {
       StageScope sc(bs, 3);
-      KRUN(ph.n_tiles, launch_hadamard<R>(N, ar.at<HadTile>(ph.tiles), ph.n_tiles, ph.max_par, ph.max_cells, ar.at<int>(ph.src_ids),
-                             ar.at<int>(ph.tgt_ids), bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
+      KRUN(ph.n_work, launch_hadamard<R>(N, ar.at<HadTile>(ph.tiles), ar.at<HadWork>(ph.work), ph.n_work,
+                                         ph.max_cells_cpc, ar.at<int>(ph.src_ids), ar.at<int>(ph.tgt_ids), bs->spec,
+                                         bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
     }
     {
       StageScope sc(bs, 4);

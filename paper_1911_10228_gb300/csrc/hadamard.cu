@@ -12,76 +12,67 @@
 // used 8 times, and the kernel spectra (indexed by d only) are the same for
 // every thread of a warp (shared-memory broadcast).
 //
-// CTA = (tile of parents) x (one chunk of T frequencies).  Shared memory holds
-// the chunk of the 343 kernel spectra of this octree level and the chunk of
+// CTA = (tile of parents) x (cpc chunks of T frequencies), 256 threads: a
+// thread is (parent slot, frequency group, chunk).  Tiles of the coarse
+// octree levels have few parents and take several chunks per CTA so every
+// CTA keeps 8 warps busy.  Shared memory holds, per chunk, the spectra of
 // every source block in the tile's region (tile grown by one parent on each
-// side, clipped to the level's bounding box; absent blocks are zero).  The
-// region is stored parity-major, [freq group][child position b][parent cell
-// q][TT], so the 32 threads of a warp (consecutive parents) read 32
-// consecutive 16-byte vectors: no bank conflicts.  Near offsets |d|_inf <= 1
-// are zeroed in shared memory on levels that exclude the near field, and
-// e = 0 is skipped there entirely.  Complex multiply-adds are written as four
-// fused multiply-adds.
+// side, clipped to the level's bounding box; absent blocks are zero), stored
+// parity-major -- [chunk][frequency group][child position b][parent cell q]
+// -- so the threads of a warp (consecutive parents) read consecutive 16-byte
+// vectors.  The host orders each tile's source list in that order, so the
+// fill is a straight copy.  Kernel spectra are read through L1: within a warp
+// every thread needs the same offset d, so each load is one broadcast.  On
+// levels that exclude the near field, e = 0 (all pairs near) is skipped and
+// the remaining near offsets |d|_inf <= 1 have zero spectra in the table
+// (set up that way for octree levels >= 1).
+// Complex multiply-adds are written as four fused multiply-adds.
 #include "common.cuh"
 #include "internal.h"
 
 namespace flgf {
 
 template <typename R, int TT>
-__global__ void __launch_bounds__(256, 2) hadamard_kernel(const HadTile* __restrict__ tiles, const int* __restrict__ src_ids,
-                                                          const int* __restrict__ tgt_ids, const cplx<R>* __restrict__ spec,
-                                                          cplx<R>* __restrict__ acc, int spec_blocks,
-                                                          const cplx<R>* __restrict__ kspec, size_t kstride) {
+__global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile* __restrict__ tiles,
+                                                                  const HadWork* __restrict__ work,
+                                                                  const int* __restrict__ src_ids,
+                                                                  const int* __restrict__ tgt_ids,
+                                                                  const cplx<R>* __restrict__ spec,
+                                                                  cplx<R>* __restrict__ acc, int spec_blocks,
+                                                                  const cplx<R>* __restrict__ kspec, size_t kstride) {
   constexpr int T = ChunkT<R>::value;
   constexpr int NG = T / TT;  // frequency groups per chunk
   static_assert(TT * sizeof(cplx<R>) == 16, "one 16-byte vector per (group, cell)");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* Ks = reinterpret_cast<cplx<R>*>(smem_raw);  // [343][T]
-  int4* Fs = reinterpret_cast<int4*>(Ks + kNOff * T);   // [NG][8][NQ] 16-byte vectors
-  const HadTile tl = tiles[blockIdx.x];
-  const int chunk = blockIdx.y;
-  const int nthreads = blockDim.x * blockDim.y;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-
-  // kernel spectra chunk (32 bytes per offset)
-  {
-    const int4* ksrc = reinterpret_cast<const int4*>(kspec + (size_t)tl.level * kstride + (size_t)chunk * kNOff * T);
-    int4* kdst = reinterpret_cast<int4*>(Ks);
-    const int4 zero4 = make_int4(0, 0, 0, 0);
-    for (int i = tid; i < kNOff * 2; i += nthreads) {
-      const int d = i >> 1;
-      const int d0 = d / 49 - 3, d1 = (d / 7) % 7 - 3, d2 = d % 7 - 3;
-      const bool near = d0 >= -1 && d0 <= 1 && d1 >= -1 && d1 <= 1 && d2 >= -1 && d2 <= 1;
-      kdst[i] = (tl.excl_near && near) ? zero4 : ksrc[i];
-    }
-  }
-  // source region chunk, natural cell order in HBM -> parity-major in shared memory
+  extern __shared__ __align__(16) int4 Fs[];  // [cpc][NG][8 NQ] 16-byte vectors
+  const HadWork wk = work[blockIdx.x];
+  const HadTile tl = tiles[wk.tile];
+  const int tid = threadIdx.x;
   const int R1 = tl.Rg[1], R2 = tl.Rg[2];
   const int NQ = tl.Rg[0] * R1 * R2;
-  const int C1 = 2 * R1, C2 = 2 * R2;
-  {
-    const int4* fsrc = reinterpret_cast<const int4*>(spec + (size_t)chunk * spec_blocks * T);
-    const int4 zero4 = make_int4(0, 0, 0, 0);
-    for (int i = tid; i < 8 * NQ * NG; i += nthreads) {
-      const int cell = i / NG, g = i % NG;
-      const int x = cell / (C1 * C2), y = (cell / C2) % C1, z = cell % C2;
-      const int b = ((x & 1) << 2) | ((y & 1) << 1) | (z & 1);
-      const int q = ((x >> 1) * R1 + (y >> 1)) * R2 + (z >> 1);
-      const int sid = src_ids[tl.src_off + cell];
-      Fs[(g * 8 + b) * NQ + q] = sid >= 0 ? fsrc[(size_t)sid * NG + g] : zero4;
+  const int S = 8 * NQ;  // slots per (chunk, group)
+
+  for (int cs = 0; cs < wk.nch; ++cs) {
+    const int4* fsrc = reinterpret_cast<const int4*>(spec + (size_t)(wk.chunk0 + cs) * spec_blocks * T);
+    int4* fdst = Fs + (size_t)cs * NG * S;
+    for (int i = tid; i < S * NG; i += kHadThreads) {
+      const int slot = i / NG, g = i % NG;
+      const int sid = src_ids[tl.src_off + slot];
+      fdst[g * S + slot] = sid >= 0 ? fsrc[(size_t)sid * NG + g] : make_int4(0, 0, 0, 0);
     }
   }
   __syncthreads();
 
+  const int pl = tid % tl.pslots;
+  const int g = (tid / tl.pslots) % NG;
+  const int cs = tid / (tl.pslots * NG);
   const int np = tl.P[0] * tl.P[1] * tl.P[2];
-  const int pl = threadIdx.x;
-  if (pl >= np) return;
-  const int g = threadIdx.y;
+  if (pl >= np || cs >= wk.nch) return;
+  const int chunk = wk.chunk0 + cs;
   const int f0 = g * TT;
   const int pq[3] = {pl / (tl.P[1] * tl.P[2]), (pl / tl.P[2]) % tl.P[1], pl % tl.P[2]};
-  // parent position inside the region
   const int q0 = tl.p0[0] + pq[0] - tl.r0[0], q1 = tl.p0[1] + pq[1] - tl.r0[1], q2 = tl.p0[2] + pq[2] - tl.r0[2];
-  const cplx<R>* Fg = reinterpret_cast<const cplx<R>*>(Fs + (size_t)g * 8 * NQ);
+  const cplx<R>* Fg = reinterpret_cast<const cplx<R>*>(Fs + (size_t)(cs * NG + g) * S);
+  const cplx<R>* Kc = kspec + (size_t)tl.level * kstride + (size_t)chunk * kNOff * T + f0;
 
   R ar[8][TT], ai[8][TT];
 #pragma unroll
@@ -96,7 +87,7 @@ __global__ void __launch_bounds__(256, 2) hadamard_kernel(const HadTile* __restr
     if (n0 < 0 || n0 >= tl.Rg[0] || n1 < 0 || n1 >= R1 || n2 < 0 || n2 >= R2) continue;
     const cplx<R>* fb = Fg + (size_t)((n0 * R1 + n1) * R2 + n2) * TT;
     // offset index of d = a - b - 2e is kbase + (a0-b0)*49 + (a1-b1)*7 + (a2-b2)
-    const cplx<R>* kb = Ks + (size_t)off_index(-2 * e0, -2 * e1, -2 * e2) * T + f0;
+    const cplx<R>* kb = Kc + (size_t)off_index(-2 * e0, -2 * e1, -2 * e2) * T;
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       const int b0 = b >> 2, b1 = (b >> 1) & 1, b2 = b & 1;
@@ -110,9 +101,12 @@ __global__ void __launch_bounds__(256, 2) hadamard_kernel(const HadTile* __restr
       for (int a = 0; a < 8; ++a) {
         const int a0 = a >> 2, a1 = (a >> 1) & 1, a2 = a & 1;
         const int dk = (a0 - b0) * 49 + (a1 - b1) * 7 + (a2 - b2);
+        // TT complex values = one 16-byte read-only load
+        const int4 kv = __ldg(reinterpret_cast<const int4*>(kb + dk * T));
+        const cplx<R>* kk = reinterpret_cast<const cplx<R>*>(&kv);
 #pragma unroll
         for (int t = 0; t < TT; ++t) {
-          const cplx<R> k = kb[dk * T + t];
+          const cplx<R> k = kk[t];
           ar[a][t] = fma(k.re, fr[t], ar[a][t]);
           ar[a][t] = fma(-k.im, fi[t], ar[a][t]);
           ai[a][t] = fma(k.re, fi[t], ai[a][t]);
@@ -136,30 +130,31 @@ __global__ void __launch_bounds__(256, 2) hadamard_kernel(const HadTile* __restr
 }
 
 template <typename R>
-cudaError_t launch_hadamard(int N, const HadTile* tiles, int ntiles, int max_parents, int max_region_cells,
+cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, int nwork, int max_cells_x_cpc,
                             const int* src_ids, const int* tgt_ids, const void* spec, void* acc, int spec_blocks,
                             const void* kspec, size_t kspec_level_stride, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
+  if (nwork <= 0) return cudaSuccess;
   constexpr int T = ChunkT<R>::value;
   constexpr int TT = (sizeof(R) == 4) ? 2 : 1;
-  const int ng = T / TT;
-  int bx = ((max_parents + 31) / 32) * 32;
-  if (bx * ng > 256) return cudaErrorInvalidConfiguration;
-  const size_t sm = sizeof(cplx<R>) * T * ((size_t)kNOff + max_region_cells);
+  const size_t sm = sizeof(cplx<R>) * T * (size_t)max_cells_x_cpc;
   if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(hadamard_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  dim3 grid(ntiles, nchunks<R>(N));
-  dim3 block(bx, ng);
-  hadamard_kernel<R, TT><<<grid, block, sm, s>>>(tiles, src_ids, tgt_ids, reinterpret_cast<const cplx<R>*>(spec),
-                                                 reinterpret_cast<cplx<R>*>(acc), spec_blocks,
-                                                 reinterpret_cast<const cplx<R>*>(kspec), kspec_level_stride);
+  static bool attr_set[2] = {false, false};
+  bool& done = attr_set[sizeof(R) == 4 ? 0 : 1];
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute(hadamard_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  hadamard_kernel<R, TT><<<nwork, kHadThreads, sm, s>>>(tiles, work, src_ids, tgt_ids,
+                                                       reinterpret_cast<const cplx<R>*>(spec),
+                                                       reinterpret_cast<cplx<R>*>(acc), spec_blocks,
+                                                       reinterpret_cast<const cplx<R>*>(kspec), kspec_level_stride);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_hadamard<float>(int, const HadTile*, int, int, int, const int*, const int*, const void*,
-                                            void*, int, const void*, size_t, cudaStream_t);
-template cudaError_t launch_hadamard<double>(int, const HadTile*, int, int, int, const int*, const int*, const void*,
-                                             void*, int, const void*, size_t, cudaStream_t);
+template cudaError_t launch_hadamard<float>(int, const HadTile*, const HadWork*, int, int, const int*, const int*,
+                                            const void*, void*, int, const void*, size_t, cudaStream_t);
+template cudaError_t launch_hadamard<double>(int, const HadTile*, const HadWork*, int, int, const int*, const int*,
+                                             const void*, void*, int, const void*, size_t, cudaStream_t);
 
 }  // namespace flgf

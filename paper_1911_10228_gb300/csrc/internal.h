@@ -32,26 +32,35 @@ template <typename R>
 cudaError_t launch_fft_inverse(int N, const void* acc, int spec_blocks, const int* sids, const int* gids,
                                const double* scales, int count, R* out, cudaStream_t s);
 // Kernel spectra of one octree level from the (2N)^3 kernel arrays (FP64 FFT),
-// stored as [chunk][343][T] in precision R.
+// stored as [chunk][343][T] in precision R; zero_near stores the 27 near
+// offsets as zero (octree levels >= 1 never use them).
 template <typename R>
-cudaError_t launch_kernel_spectra(int N, const double* karr, void* kspec_level, double* tmp, cudaStream_t s);
+cudaError_t launch_kernel_spectra(int N, const double* karr, void* kspec_level, double* tmp, int zero_near,
+                                  cudaStream_t s);
 
 // ---- a3 spectrum multiply-accumulate (hadamard.cu) ------------------------
 struct HadTile {
-  int src_off;      // offset into src id array; region cells (2 Rx)(2 Ry)(2 Rz), last axis fastest
-  int tgt_off;      // offset into tgt id array; (2 Px)(2 Py)(2 Pz) target cells
+  int src_off;      // offset into the source id list: 8 * NQ slots, parity-major (slot = b * NQ + q)
+  int tgt_off;      // offset into tgt id array; (2 Px)(2 Py)(2 Pz) target cells, last axis fastest
   int level;        // octree level k (selects the kernel spectra)
   int excl_near;    // 1 when near neighbours are not part of this level's lists
   int p0[3];        // tile parent box origin (parent coords)
   int P[3];         // tile parent box dims
   int r0[3];        // region parent box origin
-  int Rg[3];        // region parent box dims
+  int Rg[3];        // region parent box dims (NQ = Rg0 Rg1 Rg2)
+  int pslots;       // parent slots per chunk: power of two >= P0 P1 P2
+  int cpc;          // frequency chunks per CTA (pslots * groups * cpc = threads per CTA)
+};
+// Work item of the spectrum MAC: (tile, first chunk).
+struct HadWork {
+  int tile, chunk0, nch;
 };
 template <typename R>
-cudaError_t launch_hadamard(int N, const HadTile* tiles, int ntiles, int max_parents, int max_region_cells,
-                            const int* src_ids, const int* tgt_ids, const void* spec, void* acc,
-                            int spec_blocks, const void* kspec, size_t kspec_level_stride,
-                            cudaStream_t s);
+cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, int nwork, int max_cells_x_cpc,
+                            const int* src_ids, const int* tgt_ids, const void* spec, void* acc, int spec_blocks,
+                            const void* kspec, size_t kspec_level_stride, cudaStream_t s);
+// Threads per CTA of the spectrum MAC.
+constexpr int kHadThreads = 256;
 
 // ---- a1/a5 and multi-resolution stencils (stencil.cu) ----------------------
 // J1: dense 1-D Lagrange matrix [2N][N] (row = child node of the two children, column = parent node).
