@@ -667,6 +667,9 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     ph.fwd_sid = ar.add(fwd_sid);
     ph.n_tiles = (int)tiles.size();
     ph.tiles = ar.add(tiles);
+    // chunk-major order: the tiles sharing a frequency chunk run back to back,
+    // so the chunk's kernel spectra and the shared halo spectra stay in L2
+    std::stable_sort(work.begin(), work.end(), [](const HadWork& x, const HadWork& y) { return x.chunk0 < y.chunk0; });
     ph.n_work = (int)work.size();
     ph.work = ar.add(work);
     ph.src_ids = ar.add(src_ids);

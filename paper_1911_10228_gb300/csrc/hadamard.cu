@@ -51,6 +51,15 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
   const int NQ = tl.Rg[0] * R1 * R2;
   const int S = 8 * NQ;  // slots per (chunk, group)
 
+  // pull this CTA's kernel-spectrum chunks (343 x 32 bytes each) into L1
+  // while the source spectra are staged in shared memory
+  constexpr int KLINES = (kNOff * T * (int)sizeof(cplx<R>) + 127) / 128;
+  for (int i = tid; i < wk.nch * KLINES; i += kHadThreads) {
+    const int cs = i / KLINES, line = i % KLINES;
+    const char* pfx = reinterpret_cast<const char*>(kspec + (size_t)tl.level * kstride +
+                                                    (size_t)(wk.chunk0 + cs) * kNOff * T) + 128 * line;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(pfx));
+  }
   for (int cs = 0; cs < wk.nch; ++cs) {
     const int4* fsrc = reinterpret_cast<const int4*>(spec + (size_t)(wk.chunk0 + cs) * spec_blocks * T);
     int4* fdst = Fs + (size_t)cs * NG * S;
