@@ -21,8 +21,11 @@
 // parity-major -- [chunk][frequency group][child position b][parent cell q]
 // -- so the threads of a warp (consecutive parents) read consecutive 16-byte
 // vectors.  The host orders each tile's source list in that order, so the
-// fill is a straight copy.  Kernel spectra are read through L1: within a warp
-// every thread needs the same offset d, so each load is one broadcast.  On
+// fill is a straight copy (through L2 only, so it does not evict the kernel
+// spectra from L1).  Kernel spectra are read through L1: within a warp every
+// thread needs the same offset d, so each load is one broadcast; per
+// neighbour parent e the 27 distinct offsets are loaded once each and the 8
+// source spectra are held in registers.  On
 // levels that exclude the near field, e = 0 (all pairs near) is skipped and
 // the remaining near offsets |d|_inf <= 1 have zero spectra in the table
 // (set up that way for octree levels >= 1).
@@ -66,7 +69,7 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
     for (int i = tid; i < S * NG; i += kHadThreads) {
       const int slot = i / NG, g = i % NG;
       const int sid = src_ids[tl.src_off + slot];
-      fdst[g * S + slot] = sid >= 0 ? fsrc[(size_t)sid * NG + g] : make_int4(0, 0, 0, 0);
+      fdst[g * S + slot] = sid >= 0 ? __ldcg(fsrc + (size_t)sid * NG + g) : make_int4(0, 0, 0, 0);
     }
   }
   __syncthreads();
@@ -94,32 +97,36 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
     if (tl.excl_near && e == 13) continue;
     const int n0 = q0 + e0, n1 = q1 + e1, n2 = q2 + e2;
     if (n0 < 0 || n0 >= tl.Rg[0] || n1 < 0 || n1 >= R1 || n2 < 0 || n2 >= R2) continue;
+    // the 8 children b of neighbour parent p + e, TT frequencies each
     const cplx<R>* fb = Fg + (size_t)((n0 * R1 + n1) * R2 + n2) * TT;
-    // offset index of d = a - b - 2e is kbase + (a0-b0)*49 + (a1-b1)*7 + (a2-b2)
-    const cplx<R>* kb = Kc + (size_t)off_index(-2 * e0, -2 * e1, -2 * e2) * T;
+    R fr[8][TT], fi[8][TT];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int b0 = b >> 2, b1 = (b >> 1) & 1, b2 = b & 1;
-      R fr[TT], fi[TT];
+    for (int b = 0; b < 8; ++b)
 #pragma unroll
       for (int t = 0; t < TT; ++t) {
         const cplx<R> v = fb[(size_t)b * NQ * TT + t];
-        fr[t] = v.re; fi[t] = v.im;
+        fr[b][t] = v.re; fi[b][t] = v.im;
       }
+    // d = a - b - 2e takes 27 values delta - 2e (delta = a - b in {-1,0,1}^3):
+    // one kernel-spectrum load per delta, applied to every (a, b) pair with a - b = delta
+    const cplx<R>* kb = Kc + (size_t)off_index(-2 * e0, -2 * e1, -2 * e2) * T;
+#pragma unroll
+    for (int dl = 0; dl < 27; ++dl) {
+      const int l0 = dl / 9 - 1, l1 = (dl / 3) % 3 - 1, l2 = dl % 3 - 1;
+      const int4 kv = __ldg(reinterpret_cast<const int4*>(kb + (l0 * 49 + l1 * 7 + l2) * T));
+      const cplx<R>* kk = reinterpret_cast<const cplx<R>*>(&kv);
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        const int a0 = a >> 2, a1 = (a >> 1) & 1, a2 = a & 1;
-        const int dk = (a0 - b0) * 49 + (a1 - b1) * 7 + (a2 - b2);
-        // TT complex values = one 16-byte read-only load
-        const int4 kv = __ldg(reinterpret_cast<const int4*>(kb + dk * T));
-        const cplx<R>* kk = reinterpret_cast<const cplx<R>*>(&kv);
+        const int b0 = (a >> 2) - l0, b1 = ((a >> 1) & 1) - l1, b2 = (a & 1) - l2;
+        if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b2 < 0 || b2 > 1) continue;  // resolved at compile time
+        const int b = (b0 << 2) | (b1 << 1) | b2;
 #pragma unroll
         for (int t = 0; t < TT; ++t) {
           const cplx<R> k = kk[t];
-          ar[a][t] = fma(k.re, fr[t], ar[a][t]);
-          ar[a][t] = fma(-k.im, fi[t], ar[a][t]);
-          ai[a][t] = fma(k.re, fi[t], ai[a][t]);
-          ai[a][t] = fma(k.im, fr[t], ai[a][t]);
+          ar[a][t] = fma(k.re, fr[b][t], ar[a][t]);
+          ar[a][t] = fma(-k.im, fi[b][t], ar[a][t]);
+          ai[a][t] = fma(k.re, fi[b][t], ai[a][t]);
+          ai[a][t] = fma(k.im, fr[b][t], ai[a][t]);
         }
       }
     }
