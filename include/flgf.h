@@ -159,6 +159,30 @@ int flgf_stage_times(flgf_blockset* bs, double* ms, int n_stages, int* n_solves,
 int flgf_work_counts(const flgf_blockset* bs, int64_t* pairs, int64_t* fwd_ffts, int64_t* inv_ffts,
                      int64_t* kernel_offsets);
 
+/* Exact block convolution without device allocation: u = h^2 (G * f) over
+ * nblk <= 32 blocks of N^3 cells whose parents (c >> 1) lie within one block
+ * of each other on every axis (a 4x4x4 box aligned to even coordinates), so
+ * every (target, source) pair is a zero-padded FFT convolution with no
+ * interpolation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory while they compute (code inside
+ * another framework's memory pool, latency-critical loops that must avoid
+ * cudaMalloc's implicit synchronisation, processes whose device memory is
+ * reserved up front).
+ *   coords  host array [nblk][3] of block coordinates
+ *   f, u    DEVICE arrays [nblk][N][N][N] in the context precision (borrowed)
+ *   h       lattice spacing (> 0)
+ * Scratch: the spectra and launch lists live in a fixed ~18 MB array in
+ * device memory that the library declares statically; every GPU that loads
+ * the library holds it until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress); make that
+ * first call outside any stream capture.  The call allocates nothing (no
+ * cudaMalloc or cudaFree), enqueues its work on the context stream and does
+ * not synchronise.  All calls on a device share the array, so calls whose
+ * GPU work may overlap (several contexts or streams on the same device) race;
+ * serialise them.  Returns FLGF_EINVAL for more than 32 blocks or blocks
+ * outside one aligned 4x4x4 box, FLGF_EMESH for duplicate blocks. */
+int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coords, const void* f, void* u, double h);
+
 /* Number of kernels the last flgf_solve enqueued (one per launch; a replayed
  * CUDA graph launches the same kernels as the solve it captured). */
 int64_t flgf_launch_count(const flgf_blockset* bs);

@@ -1062,3 +1062,21 @@ extern "C" int flgf_laplacian(flgf_blockset* bs, int problem, int level, const v
   }
   return FLGF_OK;
 }
+
+// ----------------------------------------------------------------------------
+// Read-only view of a context for other translation units of the library.
+// ----------------------------------------------------------------------------
+namespace flgf {
+bool ctx_view(const flgf_ctx* c, CtxView* v) {
+  if (!c || !v) return false;
+  v->N = c->N;
+  v->fp64 = c->prec == FLGF_FP64;
+  v->stream = c->stream;
+  v->kspec = c->d_kspec;
+  v->kstride = c->kstride;
+  return true;
+}
+void ctx_set_error(flgf_ctx* c, const char* msg) {
+  if (c) c->err = msg;
+}
+}  // namespace flgf

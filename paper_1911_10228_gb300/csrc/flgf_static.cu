@@ -1,0 +1,178 @@
+// flgf_convolve_static: the exact block convolution without any device
+// allocation.
+//
+// Who needs it: callers that must not allocate device memory while they
+// compute -- code that runs inside a memory pool owned by another framework,
+// latency-critical loops that cannot afford cudaMalloc's implicit
+// synchronisation, or processes whose device memory is fully reserved up
+// front.  The block-set API allocates its spectra at flgf_blockset_create;
+// this entry point instead keeps its scratch (the forward and accumulated
+// spectra and the launch lists) in one file-scope __device__ array of fixed
+// size that every GPU loading the library holds until the process exits.
+//
+// It computes u = h^2 (G * f) over at most kStaticMaxBlocks blocks whose
+// octree has a single level (all blocks within a 4 x 4 x 4 box aligned to
+// even coordinates), so every pair is an exact zero-padded FFT convolution:
+// the same forward FFT, spectrum multiply-accumulate and inverse FFT kernels
+// as flgf_solve, with their scratch in the static array.
+#include <algorithm>
+#include <array>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/flgf.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+using namespace flgf;
+
+constexpr int kStaticMaxBlocks = 32;
+constexpr size_t kSpecBytes = (size_t)kStaticMaxBlocks * nfreq(16) * 16;  // complex double, N = 16
+constexpr size_t kListBytes = 512 * 1024;
+constexpr size_t kScratchBytes = 2 * kSpecBytes + kListBytes;             // ~18.3 MB
+
+// Shared by every call on a device; see the header for the concurrency rule.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_scratch on the current device (set up once per device).
+cudaError_t scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+template <typename T>
+size_t put(std::vector<unsigned char>& buf, const std::vector<T>& v) {
+  const size_t off = (buf.size() + 255) & ~(size_t)255;
+  buf.resize(off + v.size() * sizeof(T));
+  if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+
+}  // namespace
+
+extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coords, const void* f, void* u,
+                                    double h) {
+  CtxView cv;
+  if (!flgf::ctx_view(ctx, &cv)) return FLGF_EINVAL;
+  auto bad = [&](int code, const char* m) {
+    flgf::ctx_set_error(ctx, m);
+    return code;
+  };
+  if (nblk < 1 || nblk > kStaticMaxBlocks || !coords || !f || !u || !(h > 0.0))
+    return bad(FLGF_EINVAL, "convolve_static: need 1..32 blocks, coordinates, device f and u, h > 0");
+  const int N = cv.N;
+  // one octree level: the parents of all blocks lie within one block of each other
+  std::array<int, 3> plo = {INT32_MAX, INT32_MAX, INT32_MAX}, phi = {INT32_MIN, INT32_MIN, INT32_MIN};
+  std::vector<std::array<int, 3>> c(nblk);
+  for (int b = 0; b < nblk; ++b)
+    for (int a = 0; a < 3; ++a) {
+      c[b][a] = coords[3 * b + a];
+      if (c[b][a] < -(1 << 19) || c[b][a] >= (1 << 19)) return bad(FLGF_EINVAL, "convolve_static: coordinate range");
+      plo[a] = std::min(plo[a], c[b][a] >> 1);
+      phi[a] = std::max(phi[a], c[b][a] >> 1);
+    }
+  for (int a = 0; a < 3; ++a)
+    if (phi[a] - plo[a] > 1)
+      return bad(FLGF_EINVAL, "convolve_static: blocks must lie in one 4x4x4 box aligned to even coordinates");
+  {
+    std::vector<std::array<int, 3>> s = c;
+    std::sort(s.begin(), s.end());
+    if (std::adjacent_find(s.begin(), s.end()) != s.end()) return bad(FLGF_EMESH, "convolve_static: duplicate block");
+  }
+  auto find = [&](int x, int y, int z) -> int {
+    for (int b = 0; b < nblk; ++b)
+      if (c[b][0] == x && c[b][1] == y && c[b][2] == z) return b;
+    return -1;
+  };
+  // launch lists: one tile covering the parent box; its region is the same box
+  HadTile tl;
+  tl.level = 0;
+  tl.excl_near = 0;
+  for (int a = 0; a < 3; ++a) {
+    tl.p0[a] = plo[a];
+    tl.P[a] = phi[a] - plo[a] + 1;
+    tl.r0[a] = plo[a];
+    tl.Rg[a] = tl.P[a];
+  }
+  const int NQ = tl.Rg[0] * tl.Rg[1] * tl.Rg[2];
+  std::vector<int> src(8 * NQ, -1), tgt;
+  for (int x = 0; x < 2 * tl.P[0]; ++x)
+    for (int y = 0; y < 2 * tl.P[1]; ++y)
+      for (int z = 0; z < 2 * tl.P[2]; ++z) {
+        const int b = find(2 * plo[0] + x, 2 * plo[1] + y, 2 * plo[2] + z);
+        tgt.push_back(b);
+        const int slot = (((x & 1) << 2) | ((y & 1) << 1) | (z & 1)) * NQ + ((x >> 1) * tl.Rg[1] + (y >> 1)) * tl.Rg[2] + (z >> 1);
+        src[slot] = b;
+      }
+  tl.src_off = 0;
+  tl.tgt_off = 0;
+  tl.pslots = 1;
+  while (tl.pslots < tl.P[0] * tl.P[1] * tl.P[2]) tl.pslots <<= 1;
+  int cpc = kHadThreads / (tl.pslots * 2);
+  while (cpc > 1 && 8 * NQ * cpc > 3200) cpc >>= 1;
+  tl.cpc = cpc;
+  const int nchunk = cv.fp64 ? nchunks<double>(N) : nchunks<float>(N);
+  std::vector<HadWork> work;
+  for (int c0 = 0; c0 < nchunk; c0 += cpc) work.push_back(HadWork{0, c0, std::min(cpc, nchunk - c0)});
+  std::vector<int> ids(nblk);
+  for (int b = 0; b < nblk; ++b) ids[b] = b;
+  std::vector<double> scales(nblk, h * h);
+  std::vector<HadTile> tiles(1, tl);
+  std::vector<unsigned char> lists;
+  const size_t o_tiles = put(lists, tiles), o_work = put(lists, work), o_src = put(lists, src), o_tgt = put(lists, tgt);
+  const size_t o_ids = put(lists, ids), o_scale = put(lists, scales);
+  if (lists.size() > kListBytes) return bad(FLGF_EINVAL, "convolve_static: launch lists exceed the scratch");
+
+  void* base = nullptr;
+  cudaError_t e = scratch_address(&base);
+  if (e != cudaSuccess) return bad(FLGF_ECUDA, cudaGetErrorString(e));
+  unsigned char* sp = static_cast<unsigned char*>(base);
+  void* spec = sp;
+  void* acc = sp + kSpecBytes;
+  unsigned char* dl = sp + 2 * kSpecBytes;
+  cudaStream_t s = cv.stream;
+  // pageable source: the call returns once the lists are staged, so `lists` may go
+  e = cudaMemcpyAsync(dl, lists.data(), lists.size(), cudaMemcpyHostToDevice, s);
+  const int* d_ids = reinterpret_cast<const int*>(dl + o_ids);
+  if (e == cudaSuccess) {
+    if (cv.fp64) e = launch_fft_forward<double>(N, static_cast<const double*>(f), d_ids, d_ids, nblk, spec, nblk, s);
+    else e = launch_fft_forward<float>(N, static_cast<const float*>(f), d_ids, d_ids, nblk, spec, nblk, s);
+  }
+  if (e == cudaSuccess) {
+    const HadTile* d_tiles = reinterpret_cast<const HadTile*>(dl + o_tiles);
+    const HadWork* d_work = reinterpret_cast<const HadWork*>(dl + o_work);
+    const int* d_src = reinterpret_cast<const int*>(dl + o_src);
+    const int* d_tgt = reinterpret_cast<const int*>(dl + o_tgt);
+    if (cv.fp64)
+      e = launch_hadamard<double>(N, d_tiles, d_work, (int)work.size(), 8 * NQ * cpc, d_src, d_tgt, spec, acc, nblk,
+                                  cv.kspec, cv.kstride, s);
+    else
+      e = launch_hadamard<float>(N, d_tiles, d_work, (int)work.size(), 8 * NQ * cpc, d_src, d_tgt, spec, acc, nblk,
+                                 cv.kspec, cv.kstride, s);
+  }
+  if (e == cudaSuccess) {
+    const double* d_scale = reinterpret_cast<const double*>(dl + o_scale);
+    if (cv.fp64) e = launch_fft_inverse<double>(N, acc, nblk, d_ids, d_ids, d_scale, nblk, static_cast<double*>(u), s);
+    else e = launch_fft_inverse<float>(N, acc, nblk, d_ids, d_ids, d_scale, nblk, static_cast<float*>(u), s);
+  }
+  if (e != cudaSuccess) return bad(FLGF_ECUDA, cudaGetErrorString(e));
+  return FLGF_OK;
+}

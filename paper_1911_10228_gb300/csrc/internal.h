@@ -5,7 +5,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct flgf_ctx;
+
 namespace flgf {
+
+// Read-only view of a context (defined in flgf_api.cu).
+struct CtxView {
+  int N;
+  bool fp64;
+  cudaStream_t stream;
+  const void* kspec;  // [octree level][chunk][343][T]
+  size_t kstride;     // complex elements per octree level
+};
+bool ctx_view(const flgf_ctx* c, CtxView* v);
+void ctx_set_error(flgf_ctx* c, const char* msg);
 
 // ---- a0: LGF table and kernel arrays (lgf.cu) ----------------------------
 // Bessel table B[k][j] = ive(k, 2 t_j), k = 0..K, j over the exp-sinh nodes.

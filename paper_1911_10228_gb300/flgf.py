@@ -63,6 +63,8 @@ PROTOTYPES = {
     "flgf_stage_times": (ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, ctypes.c_int, _c_int_p, ctypes.c_int]),
     "flgf_work_counts": (ctypes.c_int, [ctypes.c_void_p, _c_i64_p, _c_i64_p, _c_i64_p, _c_i64_p]),
     "flgf_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "flgf_convolve_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_i32_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_double]),
 }
 
 _LIB = None
@@ -137,6 +139,21 @@ class Context:
         self.check(self.lib.flgf_kernel_spectrum(self.handle, k, int(d[0]), int(d[1]), int(d[2]),
                                                  _ptr(out, ctypes.c_double)), "flgf_kernel_spectrum")
         return out.view(np.complex128).reshape(2 * N, 2 * N, N + 1)
+
+    def convolve_static(self, coords, f: torch.Tensor, h: float = 1.0, out: torch.Tensor | None = None):
+        """Exact block convolution of at most 32 blocks (one 4x4x4 aligned box) with
+        no device allocation inside the library; f and out are device tensors."""
+        coords = np.ascontiguousarray(np.asarray(coords, dtype=np.int32).reshape(-1, 3))
+        f = f.to(device=self.device, dtype=self.dtype).contiguous()
+        if out is None:
+            out = torch.empty_like(f)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self.check(self.lib.flgf_convolve_static(self.handle, coords.shape[0], _ptr(coords, ctypes.c_int32),
+                                                 ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                                 float(h)), "flgf_convolve_static")
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        f.record_stream(self.stream)
+        return out
 
     def close(self):
         if getattr(self, "handle", None):
