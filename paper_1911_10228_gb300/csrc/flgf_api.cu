@@ -625,10 +625,10 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
               const int np = tl.P[0] * tl.P[1] * tl.P[2];
               tl.pslots = 1;
               while (tl.pslots < np) tl.pslots <<= 1;
-              int cpc = kHadThreads / (tl.pslots * 2);
-              while (cpc > 1 && 8 * NQ * cpc > 3200) cpc >>= 1;
+              int cpc = std::min(kHadMaxCpc, kHadThreads / (tl.pslots * 2));
+              while (cpc > 1 && (8 * NQ + kNOff) * cpc > 3520) cpc >>= 1;  // <= 110 KB shared
               tl.cpc = cpc;
-              ph.max_cells_cpc = std::max(ph.max_cells_cpc, 8 * NQ * cpc);
+              ph.max_cells_cpc = std::max(ph.max_cells_cpc, (8 * NQ + kNOff) * cpc);
               for (int c0 = 0; c0 < nchunk; c0 += cpc)
                 work.push_back(HadWork{(int)tiles.size(), c0, std::min(cpc, nchunk - c0)});
               tl.tgt_off = (int)tgt_ids.size();

@@ -126,8 +126,8 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
   tl.tgt_off = 0;
   tl.pslots = 1;
   while (tl.pslots < tl.P[0] * tl.P[1] * tl.P[2]) tl.pslots <<= 1;
-  int cpc = kHadThreads / (tl.pslots * 2);
-  while (cpc > 1 && 8 * NQ * cpc > 3200) cpc >>= 1;
+  int cpc = std::min(kHadMaxCpc, kHadThreads / (tl.pslots * 2));
+  while (cpc > 1 && (8 * NQ + kNOff) * cpc > 3520) cpc >>= 1;  // <= 110 KB shared
   tl.cpc = cpc;
   const int nchunk = cv.fp64 ? nchunks<double>(N) : nchunks<float>(N);
   std::vector<HadWork> work;
@@ -162,10 +162,10 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
     const int* d_src = reinterpret_cast<const int*>(dl + o_src);
     const int* d_tgt = reinterpret_cast<const int*>(dl + o_tgt);
     if (cv.fp64)
-      e = launch_hadamard<double>(N, d_tiles, d_work, (int)work.size(), 8 * NQ * cpc, d_src, d_tgt, spec, acc, nblk,
+      e = launch_hadamard<double>(N, d_tiles, d_work, (int)work.size(), (8 * NQ + kNOff) * cpc, d_src, d_tgt, spec, acc, nblk,
                                   cv.kspec, cv.kstride, s);
     else
-      e = launch_hadamard<float>(N, d_tiles, d_work, (int)work.size(), 8 * NQ * cpc, d_src, d_tgt, spec, acc, nblk,
+      e = launch_hadamard<float>(N, d_tiles, d_work, (int)work.size(), (8 * NQ + kNOff) * cpc, d_src, d_tgt, spec, acc, nblk,
                                  cv.kspec, cv.kstride, s);
   }
   if (e == cudaSuccess) {

@@ -21,11 +21,11 @@
 // parity-major -- [chunk][frequency group][child position b][parent cell q]
 // -- so the threads of a warp (consecutive parents) read consecutive 16-byte
 // vectors.  The host orders each tile's source list in that order, so the
-// fill is a straight copy (through L2 only, so it does not evict the kernel
-// spectra from L1).  Kernel spectra are read through L1: within a warp every
-// thread needs the same offset d, so each load is one broadcast; per
-// neighbour parent e the 27 distinct offsets are loaded once each and the 8
-// source spectra are held in registers.  On
+// fill is a straight copy (through L2 only).  The CTA's kernel-spectrum
+// chunks are staged in shared memory too: within a warp every thread needs
+// the same offset d, so each read is one broadcast; per neighbour parent e
+// the 27 distinct offsets are read once each and the 8 source spectra are
+// held in registers.  On
 // levels that exclude the near field, e = 0 (all pairs near) is skipped and
 // the remaining near offsets |d|_inf <= 1 have zero spectra in the table
 // (set up that way for octree levels >= 1).
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
   constexpr int T = ChunkT<R>::value;
   constexpr int NG = T / TT;  // frequency groups per chunk
   static_assert(TT * sizeof(cplx<R>) == 16, "one 16-byte vector per (group, cell)");
-  extern __shared__ __align__(16) int4 Fs[];  // [cpc][NG][8 NQ] 16-byte vectors
+  extern __shared__ __align__(16) int4 Fs[];  // [cpc][NG][8 NQ] 16-byte vectors, then [cpc][343][T] kernel spectra
   const HadWork wk = work[blockIdx.x];
   const HadTile tl = tiles[wk.tile];
   const int tid = threadIdx.x;
@@ -54,14 +54,12 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
   const int NQ = tl.Rg[0] * R1 * R2;
   const int S = 8 * NQ;  // slots per (chunk, group)
 
-  // pull this CTA's kernel-spectrum chunks (343 x 32 bytes each) into L1
-  // while the source spectra are staged in shared memory
-  constexpr int KLINES = (kNOff * T * (int)sizeof(cplx<R>) + 127) / 128;
-  for (int i = tid; i < wk.nch * KLINES; i += kHadThreads) {
-    const int cs = i / KLINES, line = i % KLINES;
-    const char* pfx = reinterpret_cast<const char*>(kspec + (size_t)tl.level * kstride +
-                                                    (size_t)(wk.chunk0 + cs) * kNOff * T) + 128 * line;
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(pfx));
+  // this CTA's kernel-spectrum chunks (343 x 32 bytes each) after the source region
+  int4* Ks = Fs + (size_t)tl.cpc * NG * S;
+  constexpr int KV = kNOff * T * (int)sizeof(cplx<R>) / 16;  // 16-byte vectors per chunk
+  for (int i = tid; i < wk.nch * KV; i += kHadThreads) {
+    const int cs = i / KV, v = i % KV;
+    Ks[i] = __ldg(reinterpret_cast<const int4*>(kspec + (size_t)tl.level * kstride + (size_t)(wk.chunk0 + cs) * kNOff * T) + v);
   }
   for (int cs = 0; cs < wk.nch; ++cs) {
     const int4* fsrc = reinterpret_cast<const int4*>(spec + (size_t)(wk.chunk0 + cs) * spec_blocks * T);
@@ -84,7 +82,7 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
   const int pq[3] = {pl / (tl.P[1] * tl.P[2]), (pl / tl.P[2]) % tl.P[1], pl % tl.P[2]};
   const int q0 = tl.p0[0] + pq[0] - tl.r0[0], q1 = tl.p0[1] + pq[1] - tl.r0[1], q2 = tl.p0[2] + pq[2] - tl.r0[2];
   const cplx<R>* Fg = reinterpret_cast<const cplx<R>*>(Fs + (size_t)(cs * NG + g) * S);
-  const cplx<R>* Kc = kspec + (size_t)tl.level * kstride + (size_t)chunk * kNOff * T + f0;
+  const cplx<R>* Kc = reinterpret_cast<const cplx<R>*>(Ks + (size_t)cs * KV) + f0;
 
   R ar[8][TT], ai[8][TT];
 #pragma unroll
@@ -113,7 +111,7 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
 #pragma unroll
     for (int dl = 0; dl < 27; ++dl) {
       const int l0 = dl / 9 - 1, l1 = (dl / 3) % 3 - 1, l2 = dl % 3 - 1;
-      const int4 kv = __ldg(reinterpret_cast<const int4*>(kb + (l0 * 49 + l1 * 7 + l2) * T));
+      const int4 kv = *reinterpret_cast<const int4*>(kb + (l0 * 49 + l1 * 7 + l2) * T);
       const cplx<R>* kk = reinterpret_cast<const cplx<R>*>(&kv);
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
@@ -152,12 +150,14 @@ cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, in
   if (nwork <= 0) return cudaSuccess;
   constexpr int T = ChunkT<R>::value;
   constexpr int TT = (sizeof(R) == 4) ? 2 : 1;
+  // per chunk: the source region cells and the 343 kernel spectra (32 bytes each)
   const size_t sm = sizeof(cplx<R>) * T * (size_t)max_cells_x_cpc;
-  if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+  if (sm > 110 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr_set[2] = {false, false};
   bool& done = attr_set[sizeof(R) == 4 ? 0 : 1];
   if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(hadamard_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    // two CTAs per SM need <= 2 x 110 KB of shared memory
+    cudaError_t e = cudaFuncSetAttribute(hadamard_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
     if (e != cudaSuccess) return e;
     done = true;
   }

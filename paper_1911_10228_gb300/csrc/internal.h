@@ -69,11 +69,12 @@ struct HadWork {
   int tile, chunk0, nch;
 };
 template <typename R>
-cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, int nwork, int max_cells_x_cpc,
+cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, int nwork, int max_units /* max (8 NQ + 343) cpc */,
                             const int* src_ids, const int* tgt_ids, const void* spec, void* acc, int spec_blocks,
                             const void* kspec, size_t kspec_level_stride, cudaStream_t s);
-// Threads per CTA of the spectrum MAC.
+// Threads per CTA of the spectrum MAC, and the most frequency chunks one CTA takes.
 constexpr int kHadThreads = 256;
+constexpr int kHadMaxCpc = 4;
 
 // ---- a1/a5 and multi-resolution stencils (stencil.cu) ----------------------
 // J1: dense 1-D Lagrange matrix [2N][N] (row = child node of the two children, column = parent node).
