@@ -129,7 +129,7 @@ struct PhaseOff {  // arena offsets and counts of one phase's launch lists
   int n_prep = 0; size_t prep_src = 0, prep_dst = 0, prep_zero = 0;
   std::vector<int> n_ant; std::vector<size_t> ant_par, ant_ch;
   int n_fwd = 0; size_t fwd_gid = 0, fwd_sid = 0;
-  int n_tiles = 0, n_work = 0, max_cells_cpc = 0; size_t tiles = 0, work = 0, src_ids = 0, tgt_ids = 0;
+  int n_tiles = 0, n_work = 0, max_cells_cpc = 0; size_t tiles = 0, work = 0, src_ids = 0, tgt_ids = 0, pmap = 0;
   int n_inv = 0; size_t inv_sid = 0, inv_gid = 0, inv_scale = 0;
   std::vector<int> n_itp; std::vector<size_t> itp_ch, itp_par, itp_cpos;
   int n_sel = 0; size_t sel_src = 0, sel_dst = 0;
@@ -512,6 +512,7 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     std::vector<HadTile> tiles;
     std::vector<HadWork> work;
     std::vector<int> src_ids, tgt_ids;
+    std::vector<int2> pmap;
     const int nchunk = ctx->prec == FLGF_FP64 ? nchunks<double>(N) : nchunks<float>(N);
     for (const auto& in : bs->inst) {
       if (in.l != l) continue;
@@ -635,6 +636,8 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
               tgt_ids.insert(tgt_ids.end(), tg.begin(), tg.end());
               tl.src_off = (int)src_ids.size();
               src_ids.insert(src_ids.end(), sg.begin(), sg.end());
+              tl.pmap_off = (int)pmap.size();
+              build_parent_map(tl, sg.data(), pmap);
               tiles.push_back(tl);
             }
       }
@@ -674,6 +677,7 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     ph.work = ar.add(work);
     ph.src_ids = ar.add(src_ids);
     ph.tgt_ids = ar.add(tgt_ids);
+    ph.pmap = ar.add(pmap);
     ph.n_inv = (int)inv_gid.size();
     ph.inv_sid = ar.add(inv_sid);
     ph.inv_gid = ar.add(inv_gid);
@@ -902,7 +906,8 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
     {
       StageScope sc(bs, 3);
       KRUN(ph.n_work, launch_hadamard<R>(N, ar.at<HadTile>(ph.tiles), ar.at<HadWork>(ph.work), ph.n_work,
-                                         ph.max_cells_cpc, ar.at<int>(ph.src_ids), ar.at<int>(ph.tgt_ids), bs->spec,
+                                         ph.max_cells_cpc, ar.at<int>(ph.src_ids), ar.at<int>(ph.tgt_ids),
+                                         ar.at<int2>(ph.pmap), bs->spec,
                                          bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
     }
     {

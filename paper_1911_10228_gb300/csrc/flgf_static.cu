@@ -135,10 +135,13 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
   std::vector<int> ids(nblk);
   for (int b = 0; b < nblk; ++b) ids[b] = b;
   std::vector<double> scales(nblk, h * h);
+  tl.pmap_off = 0;
+  std::vector<int2> pmap;
+  build_parent_map(tl, src.data(), pmap);
   std::vector<HadTile> tiles(1, tl);
   std::vector<unsigned char> lists;
   const size_t o_tiles = put(lists, tiles), o_work = put(lists, work), o_src = put(lists, src), o_tgt = put(lists, tgt);
-  const size_t o_ids = put(lists, ids), o_scale = put(lists, scales);
+  const size_t o_ids = put(lists, ids), o_scale = put(lists, scales), o_pmap = put(lists, pmap);
   if (lists.size() > kListBytes) return bad(FLGF_EINVAL, "convolve_static: launch lists exceed the scratch");
 
   void* base = nullptr;
@@ -161,11 +164,12 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
     const HadWork* d_work = reinterpret_cast<const HadWork*>(dl + o_work);
     const int* d_src = reinterpret_cast<const int*>(dl + o_src);
     const int* d_tgt = reinterpret_cast<const int*>(dl + o_tgt);
+    const int2* d_pmap = reinterpret_cast<const int2*>(dl + o_pmap);
     if (cv.fp64)
-      e = launch_hadamard<double>(N, d_tiles, d_work, (int)work.size(), (8 * NQ + kNOff) * cpc, d_src, d_tgt, spec, acc, nblk,
+      e = launch_hadamard<double>(N, d_tiles, d_work, (int)work.size(), (8 * NQ + kNOff) * cpc, d_src, d_tgt, d_pmap, spec, acc, nblk,
                                   cv.kspec, cv.kstride, s);
     else
-      e = launch_hadamard<float>(N, d_tiles, d_work, (int)work.size(), (8 * NQ + kNOff) * cpc, d_src, d_tgt, spec, acc, nblk,
+      e = launch_hadamard<float>(N, d_tiles, d_work, (int)work.size(), (8 * NQ + kNOff) * cpc, d_src, d_tgt, d_pmap, spec, acc, nblk,
                                  cv.kspec, cv.kstride, s);
   }
   if (e == cudaSuccess) {

@@ -30,6 +30,9 @@
 // the remaining near offsets |d|_inf <= 1 have zero spectra in the table
 // (set up that way for octree levels >= 1).
 // Complex multiply-adds are written as four fused multiply-adds.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -40,6 +43,7 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
                                                                   const HadWork* __restrict__ work,
                                                                   const int* __restrict__ src_ids,
                                                                   const int* __restrict__ tgt_ids,
+                                                                  const int2* __restrict__ pmap,
                                                                   const cplx<R>* __restrict__ spec,
                                                                   cplx<R>* __restrict__ acc, int spec_blocks,
                                                                   const cplx<R>* __restrict__ kspec, size_t kstride) {
@@ -72,11 +76,14 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
   }
   __syncthreads();
 
-  const int pl = tid % tl.pslots;
+  const int slot = tid % tl.pslots;
   const int g = (tid / tl.pslots) % NG;
   const int cs = tid / (tl.pslots * NG);
   const int np = tl.P[0] * tl.P[1] * tl.P[2];
-  if (pl >= np || cs >= wk.nch) return;
+  if (slot >= np || cs >= wk.nch) return;
+  const int2 pm = pmap[tl.pmap_off + slot];
+  const int pl = pm.x;          // parent index in the tile
+  const unsigned emask = pm.y;  // neighbours e that hold sources
   const int chunk = wk.chunk0 + cs;
   const int f0 = g * TT;
   const int pq[3] = {pl / (tl.P[1] * tl.P[2]), (pl / tl.P[2]) % tl.P[1], pl % tl.P[2]};
@@ -91,10 +98,9 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
     for (int t = 0; t < TT; ++t) { ar[a][t] = R(0); ai[a][t] = R(0); }
 
   for (int e = 0; e < 27; ++e) {
+    if (!((emask >> e) & 1u)) continue;  // outside the region, no sources, or e = 0 without near field
     const int e0 = e / 9 - 1, e1 = (e / 3) % 3 - 1, e2 = e % 3 - 1;
-    if (tl.excl_near && e == 13) continue;
     const int n0 = q0 + e0, n1 = q1 + e1, n2 = q2 + e2;
-    if (n0 < 0 || n0 >= tl.Rg[0] || n1 < 0 || n1 >= R1 || n2 < 0 || n2 >= R2) continue;
     // the 8 children b of neighbour parent p + e, TT frequencies each
     const cplx<R>* fb = Fg + (size_t)((n0 * R1 + n1) * R2 + n2) * TT;
     R fr[8][TT], fi[8][TT];
@@ -145,8 +151,8 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
 
 template <typename R>
 cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, int nwork, int max_cells_x_cpc,
-                            const int* src_ids, const int* tgt_ids, const void* spec, void* acc, int spec_blocks,
-                            const void* kspec, size_t kspec_level_stride, cudaStream_t s) {
+                            const int* src_ids, const int* tgt_ids, const int2* pmap, const void* spec, void* acc,
+                            int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s) {
   if (nwork <= 0) return cudaSuccess;
   constexpr int T = ChunkT<R>::value;
   constexpr int TT = (sizeof(R) == 4) ? 2 : 1;
@@ -161,7 +167,7 @@ cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, in
     if (e != cudaSuccess) return e;
     done = true;
   }
-  hadamard_kernel<R, TT><<<nwork, kHadThreads, sm, s>>>(tiles, work, src_ids, tgt_ids,
+  hadamard_kernel<R, TT><<<nwork, kHadThreads, sm, s>>>(tiles, work, src_ids, tgt_ids, pmap,
                                                        reinterpret_cast<const cplx<R>*>(spec),
                                                        reinterpret_cast<cplx<R>*>(acc), spec_blocks,
                                                        reinterpret_cast<const cplx<R>*>(kspec), kspec_level_stride);
@@ -169,8 +175,37 @@ cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, in
 }
 
 template cudaError_t launch_hadamard<float>(int, const HadTile*, const HadWork*, int, int, const int*, const int*,
-                                            const void*, void*, int, const void*, size_t, cudaStream_t);
+                                            const int2*, const void*, void*, int, const void*, size_t, cudaStream_t);
 template cudaError_t launch_hadamard<double>(int, const HadTile*, const HadWork*, int, int, const int*, const int*,
-                                             const void*, void*, int, const void*, size_t, cudaStream_t);
+                                             const int2*, const void*, void*, int, const void*, size_t, cudaStream_t);
+
+void build_parent_map(const HadTile& tl, const int* src_slots, std::vector<int2>& out) {
+  const int np = tl.P[0] * tl.P[1] * tl.P[2];
+  const int NQ = tl.Rg[0] * tl.Rg[1] * tl.Rg[2];
+  std::vector<int2> m(np);
+  for (int pl = 0; pl < np; ++pl) {
+    const int pq[3] = {pl / (tl.P[1] * tl.P[2]), (pl / tl.P[2]) % tl.P[1], pl % tl.P[2]};
+    unsigned mask = 0;
+    for (int e = 0; e < 27; ++e) {
+      if (tl.excl_near && e == 13) continue;
+      int n[3];
+      bool in = true;
+      for (int a = 0; a < 3; ++a) {
+        const int ea = (a == 0 ? e / 9 : a == 1 ? (e / 3) % 3 : e % 3) - 1;
+        n[a] = tl.p0[a] + pq[a] - tl.r0[a] + ea;
+        in &= n[a] >= 0 && n[a] < tl.Rg[a];
+      }
+      if (!in) continue;
+      const int q = (n[0] * tl.Rg[1] + n[1]) * tl.Rg[2] + n[2];
+      bool any = false;
+      for (int b = 0; b < 8; ++b) any |= src_slots[b * NQ + q] >= 0;
+      if (any) mask |= 1u << e;
+    }
+    m[pl] = make_int2(pl, (int)mask);
+  }
+  // group equal masks (stable: spatial order inside a group keeps shared reads local)
+  std::stable_sort(m.begin(), m.end(), [](const int2& x, const int2& y) { return (unsigned)x.y < (unsigned)y.y; });
+  out.insert(out.end(), m.begin(), m.end());
+}
 
 }  // namespace flgf

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 struct flgf_ctx;
 
 namespace flgf {
@@ -63,6 +65,7 @@ struct HadTile {
   int Rg[3];        // region parent box dims (NQ = Rg0 Rg1 Rg2)
   int pslots;       // parent slots per chunk: power of two >= P0 P1 P2
   int cpc;          // frequency chunks per CTA (pslots * groups * cpc = threads per CTA)
+  int pmap_off;     // offset into the parent map: per slot (parent index in the tile, 27-bit neighbour mask)
 };
 // Work item of the spectrum MAC: (tile, first chunk).
 struct HadWork {
@@ -70,8 +73,12 @@ struct HadWork {
 };
 template <typename R>
 cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, int nwork, int max_units /* max (8 NQ + 343) cpc */,
-                            const int* src_ids, const int* tgt_ids, const void* spec, void* acc, int spec_blocks,
-                            const void* kspec, size_t kspec_level_stride, cudaStream_t s);
+                            const int* src_ids, const int* tgt_ids, const int2* pmap, const void* spec, void* acc,
+                            int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s);
+// Parent map of one tile: slot order (parents grouped by neighbour mask so a
+// warp's threads visit the same neighbours) and each parent's mask of
+// neighbour parents e that hold at least one source.
+void build_parent_map(const HadTile& tl, const int* src_slots, std::vector<int2>& out);
 // Threads per CTA of the spectrum MAC, and the most frequency chunks one CTA takes.
 constexpr int kHadThreads = 256;
 constexpr int kHadMaxCpc = 4;
