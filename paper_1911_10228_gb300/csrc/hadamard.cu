@@ -203,8 +203,7 @@ void build_parent_map(const HadTile& tl, const int* src_slots, std::vector<int2>
     }
     m[pl] = make_int2(pl, (int)mask);
   }
-  // group equal masks (stable: spatial order inside a group keeps shared reads local)
-  std::stable_sort(m.begin(), m.end(), [](const int2& x, const int2& y) { return (unsigned)x.y < (unsigned)y.y; });
+  // spatial order: consecutive threads read consecutive shared-memory vectors
   out.insert(out.end(), m.begin(), m.end());
 }
 

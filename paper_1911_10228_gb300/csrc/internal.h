@@ -75,9 +75,8 @@ template <typename R>
 cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, int nwork, int max_units /* max (8 NQ + 343) cpc */,
                             const int* src_ids, const int* tgt_ids, const int2* pmap, const void* spec, void* acc,
                             int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s);
-// Parent map of one tile: slot order (parents grouped by neighbour mask so a
-// warp's threads visit the same neighbours) and each parent's mask of
-// neighbour parents e that hold at least one source.
+// Parent map of one tile: per parent slot (spatial order) the mask of
+// neighbour parents e that lie in the region and hold at least one source.
 void build_parent_map(const HadTile& tl, const int* src_slots, std::vector<int2>& out);
 // Threads per CTA of the spectrum MAC, and the most frequency chunks one CTA takes.
 constexpr int kHadThreads = 256;
