@@ -16,13 +16,24 @@ Algorithm, in the paper's order (Sec. 3, the three numbered steps):
       FLGF of all level-l sources evaluated on all level-l blocks, and one of
       the non-leaf sources only; leaf targets keep the first, non-leaf
       targets the difference (= the field of the leaf sources).
-   b. Accumulation: u~^l = v~^l + J^{l-1} u~^{l-1}.
-   c. Source correction: f^{l+1} <- f^{l+1} - L_Q^{(h_{l+1})} J^l u~^l on
+   b. Accumulation: u~^l = v~^l + J^{l-1} W^{l-1}, where W^{l-1} is the
+      field of the leaf sources of levels <= l-1 (next item).
+   c. Source correction: f^{l+1} <- f^{l+1} - L_Q^{(h_{l+1})} J^l W^l on
       every level-(l+1) block.
 3. The answer is u~^l on the leaf blocks of every level.
 
 Readings (the paper is garbled or silent here):
-* The operand of the correction is the accumulated field u~^l (the printed
+* What J^l interpolates (Sec. 3, "Regularization and Interpolation
+  operators": the interpolant is the interaction of a non-leaf octant with the
+  leaf octants only, taken over a buffer layer around the octant): the
+  leaf-source field W^l = (field of the level-l leaf sources) + J^{l-1} W^{l-1},
+  i.e. the field of the leaf sources of all levels <= l, evaluated on the
+  non-leaf blocks and their buffer of neighbouring blocks.  (On non-leaf
+  blocks W^l equals u~^l; on leaf blocks it omits the coarsened finer sources,
+  whose field the finer level computes itself.  Interpolating u~^l there
+  instead makes the interpolant jump at the coarse-fine interface, and the
+  correction turns that jump into a large spurious source.)
+* The operand of the correction is that field, J^l W^l (the printed
   "J^l f~^l" cannot be a field).  With it L_Q^{(h_{l+1})} u~^{l+1} reproduces
   f^{l+1} on the interior of level l+1 (Sec. 3, the Laplacian-free
   requirement).
@@ -178,28 +189,33 @@ def multires_solve(G, levels_coords, levels_f, N: int, n_interp: int, h0: float 
         for i, v in coarsen(lv[l + 1], f[l + 1], lv[l].coords, ~leaf[l]).items():
             f[l][i] = v
     u = [None] * L
+    w = [None] * L  # leaf-source field W^l: what J^l interpolates
     for l in range(L):
         h = h0 / (1 << l)
         op = FLGF(G, lv[l].coords, N, n_interp)
         v_all = op.apply(f[l], h=h)
         if np.any(~leaf[l]):
             f_nl = np.where((~leaf[l])[:, None, None, None], f[l], 0.0)
-            v_nl = op.apply(f_nl, h=h)
-            v = np.where(leaf[l][:, None, None, None], v_all, v_all - v_nl)
+            v_leaf = v_all - op.apply(f_nl, h=h)
         else:
-            v = v_all
+            v_leaf = v_all
+        v = np.where(leaf[l][:, None, None, None], v_all, v_leaf)
+        wl = v_leaf.copy()
         if l > 0:
             for b, c in enumerate(lv[l].coords):
-                v[b] += interp_coarse_to_fine(lv[l - 1], u[l - 1], _block_cells(c, N))
+                jw = interp_coarse_to_fine(lv[l - 1], w[l - 1], _block_cells(c, N))
+                v[b] += jw
+                wl[b] += jw
         u[l] = v
+        w[l] = wl
         if correction and l + 1 < L:
             hf = h0 / (1 << (l + 1))
             for b, c in enumerate(lv[l + 1].coords):
-                ju = interp_coarse_to_fine(lv[l], u[l], _block_cells(c, N, pad=1))
-                lap = (ju[2:, 1:-1, 1:-1] + ju[:-2, 1:-1, 1:-1] + ju[1:-1, 2:, 1:-1]
-                       + ju[1:-1, :-2, 1:-1] + ju[1:-1, 1:-1, 2:] + ju[1:-1, 1:-1, :-2]
-                       - 6.0 * ju[1:-1, 1:-1, 1:-1]) / (hf * hf)
+                jw = interp_coarse_to_fine(lv[l], w[l], _block_cells(c, N, pad=1))
+                lap = (jw[2:, 1:-1, 1:-1] + jw[:-2, 1:-1, 1:-1] + jw[1:-1, 2:, 1:-1]
+                       + jw[1:-1, :-2, 1:-1] + jw[1:-1, 1:-1, 2:] + jw[1:-1, 1:-1, :-2]
+                       - 6.0 * jw[1:-1, 1:-1, 1:-1]) / (hf * hf)
                 f[l + 1][b] -= lap
     if return_all:
-        return u, leaf, f
+        return u, leaf, f, w
     return u, leaf

@@ -110,6 +110,7 @@ struct Inst {  // one FMM over one refinement level of one problem
 struct LevelInfo {
   std::vector<I3> c;
   std::vector<uint8_t> leaf;
+  std::vector<uint8_t> ext;  // non-leaf block or a neighbour of one: where W^l is needed
   std::unordered_map<uint64_t, int> idx;
   int fw0 = 0;      // first block in fuser / fwork
   int ugid0 = 0;    // first global id of u^l (instance 0, octree level 0)
@@ -133,7 +134,9 @@ struct PhaseOff {  // arena offsets and counts of one phase's launch lists
   int n_inv = 0; size_t inv_sid = 0, inv_gid = 0, inv_scale = 0;
   std::vector<int> n_itp; std::vector<size_t> itp_ch, itp_par, itp_cpos;
   int n_sel = 0; size_t sel_src = 0, sel_dst = 0;
+  int n_selw = 0; size_t selw_src = 0, selw_dst = 0;
   int n_acc = 0; size_t acc_nbr = 0, acc_fine = 0, acc_cpos = 0;
+  int n_accw = 0; size_t accw_nbr = 0, accw_fine = 0, accw_cpos = 0;
   int n_cor = 0; size_t cor_nbr = 0, cor_fine = 0, cor_cpos = 0, cor_ih2 = 0;
   int n_crs = 0; size_t crs_coarse = 0, crs_fine = 0;  // coarsening of level l from l+1
 };
@@ -152,6 +155,7 @@ struct flgf_blockset {
   void* unodes = nullptr;
   void* fuser = nullptr;
   void* fwork = nullptr;
+  void* wfield = nullptr;  // leaf-source field W^l on non-leaf blocks and their buffer, [B][N^3]
   void* spec = nullptr;
   void* acc = nullptr;
   void* lap_in = nullptr;
@@ -355,6 +359,7 @@ extern "C" void flgf_blockset_destroy(flgf_blockset* bs) {
   cudaFree(bs->unodes);
   cudaFree(bs->fuser);
   cudaFree(bs->fwork);
+  cudaFree(bs->wfield);
   cudaFree(bs->spec);
   cudaFree(bs->acc);
   cudaFree(bs->lap_in);
@@ -436,6 +441,14 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
         }
       }
       for (size_t b = 0; b < L.c.size(); ++b) bs->dof += L.leaf[b] ? (int64_t)N3 : 0;
+      L.ext.assign(L.c.size(), 0);
+      for (size_t b = 0; b < L.c.size(); ++b) {
+        if (L.leaf[b]) continue;
+        for (int e = 0; e < 27; ++e) {
+          auto it = L.idx.find(key3(L.c[b][0] + e / 9 - 1, L.c[b][1] + (e / 3) % 3 - 1, L.c[b][2] + e % 3 - 1));
+          if (it != L.idx.end()) L.ext[it->second] = 1;
+        }
+      }
     }
     bs->Lmax = std::max(bs->Lmax, P.L);
   }
@@ -476,7 +489,7 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
         if (variant == 1) {
           for (size_t b = 0; b < L.c.size(); ++b) {
             in.is_src[0][b] = L.leaf[b];
-            if (!L.leaf[b]) {  // target: this block and its ancestors
+            if (L.ext[b]) {  // target: non-leaf blocks, their buffer, and the ancestors
               I3 c = L.c[b];
               for (size_t k = 0; k < in.lv.size(); ++k) {
                 in.need_tgt[k][in.idx[k][key3(c)]] = 1;
@@ -683,7 +696,8 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     ph.inv_gid = ar.add(inv_gid);
     ph.inv_scale = ar.add(inv_scale);
     // multi-resolution coupling lists
-    std::vector<int> sel_src, sel_dst, acc_nbr, acc_fine, acc_cpos, cor_nbr, cor_fine, cor_cpos, crs_c, crs_f;
+    std::vector<int> sel_src, sel_dst, selw_src, selw_dst, acc_nbr, acc_fine, acc_cpos, accw_nbr, accw_fine,
+        accw_cpos, cor_nbr, cor_fine, cor_cpos, crs_c, crs_f;
     std::vector<double> cor_ih2;
     for (int p = 0; p < n_problems; ++p) {
       Problem& P = bs->prob[p];
@@ -691,25 +705,38 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
       LevelInfo& L = P.lev[l];
       if (L.inst1 >= 0) {
         const Inst& i1 = bs->inst[L.inst1];
-        for (size_t b = 0; b < L.c.size(); ++b)
-          if (!L.leaf[b]) {
+        for (size_t b = 0; b < L.c.size(); ++b) {
+          if (!L.leaf[b]) {  // u on non-leaf blocks: the leaf-source field
             sel_src.push_back(i1.gid0[0] + (int)b);
             sel_dst.push_back(L.ugid0 + (int)b);
           }
+          if (L.ext[b]) {  // W^l on non-leaf blocks and their buffer
+            selw_src.push_back(i1.gid0[0] + (int)b);
+            selw_dst.push_back(L.fw0 + (int)b);
+          }
+        }
       }
+      // coarse neighbourhood of a parent as indices into W (level-block numbering)
       auto nbr27 = [&](const LevelInfo& C, const I3& parent, std::vector<int>& outv) {
         for (int e = 0; e < 27; ++e) {
           auto it = C.idx.find(key3(parent[0] + e / 9 - 1, parent[1] + (e / 3) % 3 - 1, parent[2] + e % 3 - 1));
-          outv.push_back(it == C.idx.end() ? -1 : C.ugid0 + it->second);
+          outv.push_back(it == C.idx.end() ? -1 : C.fw0 + it->second);
         }
       };
       if (l > 0) {
         const LevelInfo& C = P.lev[l - 1];
         for (size_t b = 0; b < L.c.size(); ++b) {
           const I3& c = L.c[b];
-          nbr27(C, {c[0] >> 1, c[1] >> 1, c[2] >> 1}, acc_nbr);
+          const I3 par = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
+          const int cp = ((c[0] & 1) << 2) | ((c[1] & 1) << 1) | (c[2] & 1);
+          nbr27(C, par, acc_nbr);
           acc_fine.push_back(L.ugid0 + (int)b);
-          acc_cpos.push_back(((c[0] & 1) << 2) | ((c[1] & 1) << 1) | (c[2] & 1));
+          acc_cpos.push_back(cp);
+          if (L.ext[b]) {
+            nbr27(C, par, accw_nbr);
+            accw_fine.push_back(L.fw0 + (int)b);
+            accw_cpos.push_back(cp);
+          }
         }
       }
       if (l + 1 < P.L) {
@@ -733,10 +760,17 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     ph.n_sel = (int)sel_src.size();
     ph.sel_src = ar.add(sel_src);
     ph.sel_dst = ar.add(sel_dst);
+    ph.n_selw = (int)selw_src.size();
+    ph.selw_src = ar.add(selw_src);
+    ph.selw_dst = ar.add(selw_dst);
     ph.n_acc = (int)acc_fine.size();
     ph.acc_nbr = ar.add(acc_nbr);
     ph.acc_fine = ar.add(acc_fine);
     ph.acc_cpos = ar.add(acc_cpos);
+    ph.n_accw = (int)accw_fine.size();
+    ph.accw_nbr = ar.add(accw_nbr);
+    ph.accw_fine = ar.add(accw_fine);
+    ph.accw_cpos = ar.add(accw_cpos);
     ph.n_cor = (int)cor_fine.size();
     ph.cor_nbr = ar.add(cor_nbr);
     ph.cor_fine = ar.add(cor_fine);
@@ -771,6 +805,7 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
   if (e == cudaSuccess) e = alloc(&bs->unodes, rs * N3 * bs->G);
   if (e == cudaSuccess) e = alloc(&bs->fuser, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->fwork, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = alloc(&bs->wfield, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->spec, 2 * rs * NW * bs->max_phase_blocks);
   if (e == cudaSuccess) e = alloc(&bs->acc, 2 * rs * NW * bs->max_phase_blocks);
   if (e == cudaSuccess) e = alloc(&bs->lap_in, rs * N3 * bs->max_level_blocks);
@@ -923,12 +958,19 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
     }
     {
       StageScope sc(bs, 6);
-      KRUN(ph.n_sel, launch_copy_blocks<R>(N, unodes, ar.at<int>(ph.sel_src), unodes, ar.at<int>(ph.sel_dst), nullptr, ph.n_sel, s));
-      KRUN(ph.n_acc, launch_cf_interp<R>(N, unodes, ar.at<int>(ph.acc_nbr), ar.at<int>(ph.acc_fine), ar.at<int>(ph.acc_cpos),
-                              ph.n_acc, unodes, 0, nullptr, bs->d_err, s));
+      R* wf = (R*)bs->wfield;
+      KRUN(ph.n_sel, launch_copy_blocks<R>(N, unodes, ar.at<int>(ph.sel_src), unodes, ar.at<int>(ph.sel_dst), nullptr,
+                                           ph.n_sel, s));
+      KRUN(ph.n_selw, launch_copy_blocks<R>(N, unodes, ar.at<int>(ph.selw_src), wf, ar.at<int>(ph.selw_dst), nullptr,
+                                            ph.n_selw, s));
+      // accumulation from the coarser level's leaf-source field W^{l-1}
+      KRUN(ph.n_acc, launch_cf_interp<R>(N, wf, ar.at<int>(ph.acc_nbr), ar.at<int>(ph.acc_fine), ar.at<int>(ph.acc_cpos),
+                                         ph.n_acc, unodes, 0, nullptr, bs->d_err, s));
+      KRUN(ph.n_accw, launch_cf_interp<R>(N, wf, ar.at<int>(ph.accw_nbr), ar.at<int>(ph.accw_fine),
+                                          ar.at<int>(ph.accw_cpos), ph.n_accw, wf, 0, nullptr, bs->d_err, s));
       if (bs->correction)
-        KRUN(ph.n_cor, launch_cf_interp<R>(N, unodes, ar.at<int>(ph.cor_nbr), ar.at<int>(ph.cor_fine), ar.at<int>(ph.cor_cpos),
-                                ph.n_cor, fwork, 1, ar.at<double>(ph.cor_ih2), bs->d_err, s));
+        KRUN(ph.n_cor, launch_cf_interp<R>(N, wf, ar.at<int>(ph.cor_nbr), ar.at<int>(ph.cor_fine), ar.at<int>(ph.cor_cpos),
+                                           ph.n_cor, fwork, 1, ar.at<double>(ph.cor_ih2), bs->d_err, s));
     }
   }
 #undef KRUN
