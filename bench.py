@@ -67,7 +67,8 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while a timed
+    region runs; samples accumulate over several regions (start/stop)."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -76,31 +77,32 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.lines = []
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
-        return self
 
-    def __exit__(self, *a):
-        self.lines = []
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines += [l for l in out.splitlines() if l.strip()]
+        self.proc = None
 
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
+        for l in self.lines:
             p = [x.strip() for x in l.split(",")]
             if len(p) < 9:
                 continue
@@ -210,6 +212,7 @@ def run_ours(a, rank, world, dist):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     res = {}
+    sampler = ClockSampler(dev)  # covers the timed regions of every precision
     precs = [p for p in a.precisions.split(",") if p]
     if "fp32" not in precs:
         raise SystemExit("the headline value is the FP32 form: --precisions must include fp32")
@@ -227,15 +230,15 @@ def run_ours(a, rank, world, dist):
         if dist:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        sampler = ClockSampler(dev)
-        with sampler:
-            for s0, s1 in evs:
-                with torch.cuda.stream(ctx.stream):
-                    flush.zero_()
-                s0.record(ctx.stream)
-                bs.solve()
-                s1.record(ctx.stream)
-            torch.cuda.synchronize()
+        sampler.start()
+        for s0, s1 in evs:
+            with torch.cuda.stream(ctx.stream):
+                flush.zero_()
+            s0.record(ctx.stream)
+            bs.solve()
+            s1.record(ctx.stream)
+        torch.cuda.synchronize()
+        sampler.stop()
         if dist:
             torch.distributed.barrier()
         step_ms = [s0.elapsed_time(s1) for s0, s1 in evs]
@@ -246,7 +249,7 @@ def run_ours(a, rank, world, dist):
         bs.set_option(F.OPT_TIMING, 0)
         res[prec] = {
             "ms_per_step": float(total.item()) / steps, "steps": steps, "launches": bs.launch_count(),
-            "stages_ms": {k: v / max(n_timed, 1) for k, v in stage.items()}, "clocks": sampler.summary(),
+            "stages_ms": {k: v / max(n_timed, 1) for k, v in stage.items()},
             "work": bs.work_counts(), "ctx": ctx, "bs": bs,
         }
         res[prec]["u"] = bs.potential(0, 0).double().cpu().numpy()
@@ -346,7 +349,7 @@ def run_ours(a, rank, world, dist):
             "value": dof * world / (e2e_ms_step / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": nbytes,
             "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms_step},
         "gpu_launches": res["fp32"]["launches"] * a.steps,
-        "clocks": res["fp32"]["clocks"],
+        "clocks": sampler.summary(),
     }
     if rank == 0:
         print(json.dumps(line))
