@@ -138,6 +138,21 @@ int flgf_get_potential(flgf_blockset* bs, int problem, int level, void* u, int w
  * check omega_h = L_Q Psi_h).  u and out: [nblk][N][N][N]. */
 int flgf_laplacian(flgf_blockset* bs, int problem, int level, const void* u, void* out, int where);
 
+/* Adjoint of the solve, for gradients (the paper has no adjoint; it follows
+ * from the linear steps of Sec. 2.1 and Sec. 3).  The solve is linear,
+ * u = A f with f the user sources of every (problem, level) (values on
+ * non-leaf blocks ignored) and u the returned potentials; for adjoint seeds g
+ * (one per (problem, level), [nblk][N][N][N], zero where the loss does not
+ * look) flgf_solve_adjoint computes A^T g: the transposes of the correction,
+ * accumulation, selection and coarsening steps in reverse order, and the FMMs
+ * (symmetric: R = J^T and G(n) = G(-n)), the leaf-only one with its source
+ * and target sets swapped.  The gradient of a loss with dL/du = g is then
+ * dL/df = A^T g, zero on non-leaf blocks.  Seeds persist until reloaded.
+ * Enqueued on the context stream; the source correction option applies. */
+int flgf_load_adjoint(flgf_blockset* bs, int problem, int level, const void* g, int where);
+int flgf_solve_adjoint(flgf_blockset* bs);
+int flgf_get_gradient(flgf_blockset* bs, int problem, int level, void* out, int where);
+
 /* Options of a block set. */
 enum {
   FLGF_OPT_CORRECTION = 1,  /* 1 (default): source correction of Sec. 3 on; 0: off */

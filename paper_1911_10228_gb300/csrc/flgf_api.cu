@@ -143,11 +143,24 @@ struct PhaseOff {  // arena offsets and counts of one phase's launch lists
 
 }  // namespace
 
+namespace {
+struct AdjOff {  // adjoint lists of one phase (level), besides its FMM lists
+  int n_prep = 0; size_t prep_dst = 0, prep_s1 = 0, prep_s2 = 0;   // nodes = gseed(masked) + gW(ext)
+  int n_gacc = 0; size_t gacc_dst = 0, gacc_s1 = 0, gacc_s2 = 0;   // gf += A^T results
+  int n_gtmp = 0; size_t gtmp_dst = 0, gtmp_s1 = 0, gtmp_s2 = 0;   // gtmp = gseed + gW(ext)
+  int n_cf0 = 0; size_t cf0_nbr = 0, cf0_fine = 0, cf0_cpos = 0;   // gW^{l-1} += J^T gtmp
+  int n_cf1 = 0; size_t cf1_nbr = 0, cf1_fine = 0, cf1_cpos = 0, cf1_ih2 = 0;  // gW^l += (L J)^T gf^{l+1}
+};
+}  // namespace
+
 struct flgf_blockset {
   flgf_ctx* ctx = nullptr;
   std::vector<Problem> prob;
   std::vector<Inst> inst;
+  std::vector<Inst> adj_inst;   // transposed leaf-only instances (sources: non-leaf + buffer, targets: leaf)
   std::vector<PhaseOff> ph;
+  std::vector<PhaseOff> aph;    // FMM lists of the adjoint
+  std::vector<AdjOff> adj;
   int Lmax = 0, G = 0, B = 0, max_phase_blocks = 0, max_level_blocks = 0;
   int64_t dof = 0, pairs = 0, n_fwd = 0, n_inv = 0, n_koff = 0;
   Arena ar;
@@ -156,6 +169,11 @@ struct flgf_blockset {
   void* fuser = nullptr;
   void* fwork = nullptr;
   void* wfield = nullptr;  // leaf-source field W^l on non-leaf blocks and their buffer, [B][N^3]
+  void* gseed = nullptr;   // adjoint of u (loaded by the caller), [B][N^3]
+  void* gW = nullptr;      // adjoint of W, [B][N^3]
+  void* gf = nullptr;      // adjoint of the level sources -> the gradient, [B][N^3]
+  void* gtmp = nullptr;    // [B][N^3]
+  bool adj_solved = false;
   void* spec = nullptr;
   void* acc = nullptr;
   void* lap_in = nullptr;
@@ -360,6 +378,10 @@ extern "C" void flgf_blockset_destroy(flgf_blockset* bs) {
   cudaFree(bs->fuser);
   cudaFree(bs->fwork);
   cudaFree(bs->wfield);
+  cudaFree(bs->gseed);
+  cudaFree(bs->gW);
+  cudaFree(bs->gf);
+  cudaFree(bs->gtmp);
   cudaFree(bs->spec);
   cudaFree(bs->acc);
   cudaFree(bs->lap_in);
@@ -511,13 +533,13 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
   // ---- launch lists ----------------------------------------------------------
   Arena& ar = bs->ar;
   const int TP[3] = {4, 4, 8};  // tile size in parents (<= 128 parents: 256 threads, two CTAs per SM)
-  for (int l = 0; l < bs->Lmax; ++l) {
-    PhaseOff& ph = bs->ph[l];
+  // FMM launch lists of phase l for the given instances (their is_src /
+  // need_tgt masks select sources and targets)
+  auto build_fmm = [&](int l, const std::vector<const Inst*>& insts, PhaseOff& ph, bool count) {
     std::vector<int> prep_src, prep_dst;
     std::vector<uint8_t> prep_zero;
     int maxtop = 0;
-    for (const auto& in : bs->inst)
-      if (in.l == l) maxtop = std::max(maxtop, in.top);
+    for (const Inst* in : insts) maxtop = std::max(maxtop, in->top);
     std::vector<std::vector<int>> ant_par(maxtop + 1), ant_ch(maxtop + 1);
     std::vector<std::vector<int>> itp_ch(maxtop + 1), itp_par(maxtop + 1), itp_cpos(maxtop + 1);
     std::vector<int> fwd_gid, fwd_sid, inv_sid, inv_gid;
@@ -527,8 +549,8 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     std::vector<int> src_ids, tgt_ids;
     std::vector<int2> pmap;
     const int nchunk = ctx->prec == FLGF_FP64 ? nchunks<double>(N) : nchunks<float>(N);
-    for (const auto& in : bs->inst) {
-      if (in.l != l) continue;
+    for (const Inst* inp : insts) {
+      const Inst& in = *inp;
       const LevelInfo& L = bs->prob[in.p].lev[l];
       for (size_t b = 0; b < L.c.size(); ++b) {
         prep_src.push_back(L.fw0 + (int)b);
@@ -631,7 +653,7 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
                             if (std::abs((sc[a] >> 1) - (tc[a] >> 1)) > 1) inlist = false;
                             if (std::abs(sc[a] - tc[a]) > 1) near = false;
                           }
-                          if (inlist && !(excl && near)) bs->pairs++;
+                          if (count && inlist && !(excl && near)) bs->pairs++;
                         }
                   }
               // threads: (parent slot, frequency group, chunk); small tiles take
@@ -655,9 +677,11 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
             }
       }
     }
-    bs->n_fwd += (int64_t)fwd_gid.size();
-    bs->n_inv += (int64_t)inv_gid.size();
-    for (int k = 0; k <= maxtop; ++k) bs->n_koff += kNOff;
+    if (count) {
+      bs->n_fwd += (int64_t)fwd_gid.size();
+      bs->n_inv += (int64_t)inv_gid.size();
+      for (int k = 0; k <= maxtop; ++k) bs->n_koff += kNOff;
+    }
     ph.n_prep = (int)prep_src.size();
     ph.prep_src = ar.add(prep_src);
     ph.prep_dst = ar.add(prep_dst);
@@ -695,6 +719,13 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     ph.inv_sid = ar.add(inv_sid);
     ph.inv_gid = ar.add(inv_gid);
     ph.inv_scale = ar.add(inv_scale);
+  };
+  for (int l = 0; l < bs->Lmax; ++l) {
+    PhaseOff& ph = bs->ph[l];
+    std::vector<const Inst*> insts;
+    for (const auto& in : bs->inst)
+      if (in.l == l) insts.push_back(&in);
+    build_fmm(l, insts, ph, true);
     // multi-resolution coupling lists
     std::vector<int> sel_src, sel_dst, selw_src, selw_dst, acc_nbr, acc_fine, acc_cpos, accw_nbr, accw_fine,
         accw_cpos, cor_nbr, cor_fine, cor_cpos, crs_c, crs_f;
@@ -780,6 +811,99 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     ph.crs_coarse = ar.add(crs_c);
     ph.crs_fine = ar.add(crs_f);
   }
+  // ---- adjoint: transposed leaf-only instances and lists --------------------
+  bs->aph.resize(bs->Lmax);
+  bs->adj.resize(bs->Lmax);
+  bs->adj_inst.reserve(bs->inst.size());
+  for (const auto& in : bs->inst) {
+    if (in.variant != 1) continue;
+    Inst t = in;  // same octree and global ids as the forward leaf-only instance
+    const LevelInfo& L = bs->prob[in.p].lev[in.l];
+    for (size_t k = 0; k < t.lv.size(); ++k) t.need_tgt[k].assign(t.lv[k].size(), 0);
+    for (size_t b = 0; b < L.c.size(); ++b) {
+      t.is_src[0][b] = L.ext[b];
+      if (L.leaf[b]) {
+        I3 c = L.c[b];
+        for (size_t k = 0; k < t.lv.size(); ++k) {
+          t.need_tgt[k][t.idx[k][key3(c)]] = 1;
+          c = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
+        }
+      }
+    }
+    t.variant = 2;
+    bs->adj_inst.push_back(std::move(t));
+  }
+  for (int l = 0; l < bs->Lmax; ++l) {
+    std::vector<const Inst*> insts;
+    for (const auto& in : bs->inst)
+      if (in.l == l && in.variant == 0) insts.push_back(&in);
+    for (const auto& in : bs->adj_inst)
+      if (in.l == l) insts.push_back(&in);
+    bs->aph[l].gid_begin = bs->ph[l].gid_begin;
+    bs->aph[l].nblocks = bs->ph[l].nblocks;
+    build_fmm(l, insts, bs->aph[l], false);
+    AdjOff& ao = bs->adj[l];
+    std::vector<int> pd, p1, p2, gd, g1, g2, td, t1, t2, c0n, c0f, c0c, c1n, c1f, c1c;
+    std::vector<double> c1h;
+    for (int p = 0; p < n_problems; ++p) {
+      Problem& P = bs->prob[p];
+      if (l >= P.L) continue;
+      LevelInfo& L = P.lev[l];
+      const Inst& i0 = bs->inst[L.inst0];
+      const bool has1 = L.inst1 >= 0;
+      const int g1base = has1 ? bs->inst[L.inst1].gid0[0] : -1;
+      for (size_t b = 0; b < L.c.size(); ++b) {
+        const int fb = L.fw0 + (int)b;
+        pd.push_back(i0.gid0[0] + (int)b);  // A^T applied to the leaf part of the adjoint of u
+        p1.push_back(L.leaf[b] ? fb : -1);
+        p2.push_back(-1);
+        if (has1) {                          // A^T (P_leaf) applied to the adjoint of the leaf-source field
+          pd.push_back(g1base + (int)b);
+          p1.push_back(L.leaf[b] ? -1 : fb);
+          p2.push_back(L.ext[b] ? fb : -1);
+        }
+        gd.push_back(fb);
+        g1.push_back(i0.gid0[0] + (int)b);
+        g2.push_back(has1 && L.leaf[b] ? g1base + (int)b : -1);
+        if (l > 0) {
+          td.push_back(fb);
+          t1.push_back(fb);
+          t2.push_back(L.ext[b] ? fb : -1);
+        }
+      }
+      auto nbr27 = [&](const LevelInfo& C, const I3& parent, std::vector<int>& outv) {
+        for (int e = 0; e < 27; ++e) {
+          auto it = C.idx.find(key3(parent[0] + e / 9 - 1, parent[1] + (e / 3) % 3 - 1, parent[2] + e % 3 - 1));
+          outv.push_back(it == C.idx.end() ? -1 : C.fw0 + it->second);
+        }
+      };
+      if (l > 0) {
+        const LevelInfo& C = P.lev[l - 1];
+        for (size_t b = 0; b < L.c.size(); ++b) {
+          const I3& c = L.c[b];
+          nbr27(C, {c[0] >> 1, c[1] >> 1, c[2] >> 1}, c0n);
+          c0f.push_back(L.fw0 + (int)b);
+          c0c.push_back(((c[0] & 1) << 2) | ((c[1] & 1) << 1) | (c[2] & 1));
+        }
+      }
+      if (l + 1 < P.L) {
+        const LevelInfo& Fl = P.lev[l + 1];
+        for (size_t b = 0; b < Fl.c.size(); ++b) {
+          const I3& c = Fl.c[b];
+          nbr27(L, {c[0] >> 1, c[1] >> 1, c[2] >> 1}, c1n);
+          c1f.push_back(Fl.fw0 + (int)b);
+          c1c.push_back(((c[0] & 1) << 2) | ((c[1] & 1) << 1) | (c[2] & 1));
+          c1h.push_back(1.0 / (Fl.h * Fl.h));
+        }
+      }
+    }
+    ao.n_prep = (int)pd.size(); ao.prep_dst = ar.add(pd); ao.prep_s1 = ar.add(p1); ao.prep_s2 = ar.add(p2);
+    ao.n_gacc = (int)gd.size(); ao.gacc_dst = ar.add(gd); ao.gacc_s1 = ar.add(g1); ao.gacc_s2 = ar.add(g2);
+    ao.n_gtmp = (int)td.size(); ao.gtmp_dst = ar.add(td); ao.gtmp_s1 = ar.add(t1); ao.gtmp_s2 = ar.add(t2);
+    ao.n_cf0 = (int)c0f.size(); ao.cf0_nbr = ar.add(c0n); ao.cf0_fine = ar.add(c0f); ao.cf0_cpos = ar.add(c0c);
+    ao.n_cf1 = (int)c1f.size(); ao.cf1_nbr = ar.add(c1n); ao.cf1_fine = ar.add(c1f); ao.cf1_cpos = ar.add(c1c);
+    ao.cf1_ih2 = ar.add(c1h);
+  }
   // face neighbours for the Laplacian
   for (auto& P : bs->prob)
     for (auto& L : P.lev) {
@@ -806,6 +930,11 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
   if (e == cudaSuccess) e = alloc(&bs->fuser, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->fwork, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->wfield, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = alloc(&bs->gseed, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = alloc(&bs->gW, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = alloc(&bs->gf, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = alloc(&bs->gtmp, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = cudaMemset(bs->gseed, 0, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->spec, 2 * rs * NW * bs->max_phase_blocks);
   if (e == cudaSuccess) e = alloc(&bs->acc, 2 * rs * NW * bs->max_phase_blocks);
   if (e == cudaSuccess) e = alloc(&bs->lap_in, rs * N3 * bs->max_level_blocks);
@@ -897,6 +1026,114 @@ struct StageScope {
 };
 
 template <typename R>
+cudaError_t enqueue_fmm(flgf_blockset* bs, const PhaseOff& ph) {
+  flgf_ctx* c = bs->ctx;
+  const int N = c->N;
+  cudaStream_t s = c->stream;
+  const Arena& ar = bs->ar;
+  R* nodes = (R*)bs->nodes;
+  R* unodes = (R*)bs->unodes;
+  cudaError_t e;
+#define KRUN(n, x)                              \
+  do {                                          \
+    if ((n) > 0) bs->launches++;                \
+    if ((e = (x)) != cudaSuccess) return e;     \
+  } while (0)
+  const int maxtop = (int)ph.n_ant.size() - 1;
+  {
+    StageScope sc(bs, 1);
+    for (int k = 1; k <= maxtop; ++k)
+      KRUN(ph.n_ant[k], launch_anterp<R>(N, c->nI, c->d_J1, ar.at<int>(ph.ant_par[k]), ar.at<int>(ph.ant_ch[k]),
+                                         ph.n_ant[k], nodes, s));
+  }
+  {
+    StageScope sc(bs, 2);
+    KRUN(ph.n_fwd, launch_fft_forward<R>(N, nodes, ar.at<int>(ph.fwd_gid), ar.at<int>(ph.fwd_sid), ph.n_fwd, bs->spec,
+                                         ph.nblocks, s));
+  }
+  {
+    StageScope sc(bs, 3);
+    KRUN(ph.n_work, launch_hadamard<R>(N, ar.at<HadTile>(ph.tiles), ar.at<HadWork>(ph.work), ph.n_work,
+                                       ph.max_cells_cpc, ar.at<int>(ph.src_ids), ar.at<int>(ph.tgt_ids),
+                                       ar.at<int2>(ph.pmap), bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
+  }
+  {
+    StageScope sc(bs, 4);
+    KRUN(ph.n_inv, launch_fft_inverse<R>(N, bs->acc, ph.nblocks, ar.at<int>(ph.inv_sid), ar.at<int>(ph.inv_gid),
+                                         ar.at<double>(ph.inv_scale), ph.n_inv, unodes, s));
+  }
+  {
+    StageScope sc(bs, 5);
+    for (int k = maxtop - 1; k >= 0; --k)
+      KRUN(ph.n_itp[k], launch_interp_add<R>(N, c->nI, c->d_J1, ar.at<int>(ph.itp_ch[k]), ar.at<int>(ph.itp_par[k]),
+                                             ar.at<int>(ph.itp_cpos[k]), ph.n_itp[k], unodes, s));
+  }
+#undef KRUN
+  return cudaSuccess;
+}
+
+// Adjoint of the solve: the transposes of Sec. 3's steps in reverse order
+// (correction, FMMs -- symmetric, with source and target masks swapped for
+// the leaf-only one -- selection, accumulation, then the coarsening).
+template <typename R>
+cudaError_t enqueue_adjoint(flgf_blockset* bs) {
+  flgf_ctx* c = bs->ctx;
+  const int N = c->N;
+  cudaStream_t s = c->stream;
+  const Arena& ar = bs->ar;
+  const size_t N3 = (size_t)N * N * N;
+  R* nodes = (R*)bs->nodes;
+  R* unodes = (R*)bs->unodes;
+  R* gseed = (R*)bs->gseed;
+  R* gW = (R*)bs->gW;
+  R* gf = (R*)bs->gf;
+  R* gtmp = (R*)bs->gtmp;
+  cudaError_t e;
+#define RUN(x) \
+  if ((e = (x)) != cudaSuccess) return e;
+#define KRUN(n, x)                              \
+  do {                                          \
+    if ((n) > 0) bs->launches++;                \
+    if ((e = (x)) != cudaSuccess) return e;     \
+  } while (0)
+  bs->launches = 0;
+  RUN(cudaMemsetAsync(gW, 0, sizeof(R) * N3 * bs->B, s));
+  RUN(cudaMemsetAsync(gf, 0, sizeof(R) * N3 * bs->B, s));
+  for (int l = bs->Lmax - 1; l >= 0; --l) {
+    const AdjOff& ao = bs->adj[l];
+    {
+      StageScope sc(bs, 6);
+      if (bs->correction)
+        KRUN(ao.n_cf1, launch_cf_interp_adjoint<R>(N, gW, ar.at<int>(ao.cf1_nbr), gf, ar.at<int>(ao.cf1_fine),
+                                                   ar.at<int>(ao.cf1_cpos), ao.n_cf1, 1, ar.at<double>(ao.cf1_ih2),
+                                                   bs->d_err, s));
+      KRUN(ao.n_prep, launch_combine_blocks<R>(N, nodes, ar.at<int>(ao.prep_dst), gseed, ar.at<int>(ao.prep_s1), gW,
+                                               ar.at<int>(ao.prep_s2), 0, ao.n_prep, s));
+    }
+    if ((e = enqueue_fmm<R>(bs, bs->aph[l])) != cudaSuccess) return e;
+    {
+      StageScope sc(bs, 6);
+      KRUN(ao.n_gacc, launch_combine_blocks<R>(N, gf, ar.at<int>(ao.gacc_dst), unodes, ar.at<int>(ao.gacc_s1), unodes,
+                                               ar.at<int>(ao.gacc_s2), 1, ao.n_gacc, s));
+      KRUN(ao.n_gtmp, launch_combine_blocks<R>(N, gtmp, ar.at<int>(ao.gtmp_dst), gseed, ar.at<int>(ao.gtmp_s1), gW,
+                                               ar.at<int>(ao.gtmp_s2), 0, ao.n_gtmp, s));
+      KRUN(ao.n_cf0, launch_cf_interp_adjoint<R>(N, gW, ar.at<int>(ao.cf0_nbr), gtmp, ar.at<int>(ao.cf0_fine),
+                                                 ar.at<int>(ao.cf0_cpos), ao.n_cf0, 0, nullptr, bs->d_err, s));
+    }
+  }
+  {
+    StageScope sc(bs, 0);
+    for (int l = 0; l + 1 < bs->Lmax; ++l) {
+      const PhaseOff& ph = bs->ph[l];
+      KRUN(ph.n_crs, launch_coarsen_adjoint<R>(N, gf, ar.at<int>(ph.crs_fine), ar.at<int>(ph.crs_coarse), ph.n_crs, s));
+    }
+  }
+#undef KRUN
+#undef RUN
+  return cudaSuccess;
+}
+
+template <typename R>
 cudaError_t enqueue_solve(flgf_blockset* bs) {
   flgf_ctx* c = bs->ctx;
   const int N = c->N;
@@ -929,33 +1166,9 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
     {
       StageScope sc(bs, 1);
       KRUN(ph.n_prep, launch_copy_blocks<R>(N, fwork, ar.at<int>(ph.prep_src), nodes, ar.at<int>(ph.prep_dst),
-                                ar.at<uint8_t>(ph.prep_zero), ph.n_prep, s));
-      for (int k = 1; k <= maxtop; ++k)
-        KRUN(ph.n_ant[k], launch_anterp<R>(N, c->nI, c->d_J1, ar.at<int>(ph.ant_par[k]), ar.at<int>(ph.ant_ch[k]), ph.n_ant[k], nodes, s));
+                                            ar.at<uint8_t>(ph.prep_zero), ph.n_prep, s));
     }
-    {
-      StageScope sc(bs, 2);
-      KRUN(ph.n_fwd, launch_fft_forward<R>(N, nodes, ar.at<int>(ph.fwd_gid), ar.at<int>(ph.fwd_sid), ph.n_fwd, bs->spec,
-                                ph.nblocks, s));
-    }
-    {
-      StageScope sc(bs, 3);
-      KRUN(ph.n_work, launch_hadamard<R>(N, ar.at<HadTile>(ph.tiles), ar.at<HadWork>(ph.work), ph.n_work,
-                                         ph.max_cells_cpc, ar.at<int>(ph.src_ids), ar.at<int>(ph.tgt_ids),
-                                         ar.at<int2>(ph.pmap), bs->spec,
-                                         bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
-    }
-    {
-      StageScope sc(bs, 4);
-      KRUN(ph.n_inv, launch_fft_inverse<R>(N, bs->acc, ph.nblocks, ar.at<int>(ph.inv_sid), ar.at<int>(ph.inv_gid),
-                                ar.at<double>(ph.inv_scale), ph.n_inv, unodes, s));
-    }
-    {
-      StageScope sc(bs, 5);
-      for (int k = maxtop - 1; k >= 0; --k)
-        KRUN(ph.n_itp[k], launch_interp_add<R>(N, c->nI, c->d_J1, ar.at<int>(ph.itp_ch[k]), ar.at<int>(ph.itp_par[k]),
-                                 ar.at<int>(ph.itp_cpos[k]), ph.n_itp[k], unodes, s));
-    }
+    if ((e = enqueue_fmm<R>(bs, ph)) != cudaSuccess) return e;
     {
       StageScope sc(bs, 6);
       R* wf = (R*)bs->wfield;
@@ -1062,6 +1275,41 @@ extern "C" int flgf_stage_times(flgf_blockset* bs, double* ms, int n_stages, int
     for (double& v : bs->stage_ms) v = 0.0;
     bs->timed_solves = 0;
   }
+  return FLGF_OK;
+}
+
+extern "C" int flgf_load_adjoint(flgf_blockset* bs, int problem, int level, const void* g, int where) {
+  if (!bs || !g || (where != FLGF_HOST && where != FLGF_DEVICE)) return FLGF_EINVAL;
+  flgf_ctx* ctx = bs->ctx;
+  if (check_pl(bs, problem, level) != FLGF_OK) return fail(ctx, FLGF_EINVAL, "load_adjoint: bad problem/level");
+  const LevelInfo& L = bs->prob[problem].lev[level];
+  const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4, N3 = (size_t)ctx->N * ctx->N * ctx->N;
+  CK(cudaMemcpyAsync((char*)bs->gseed + rs * N3 * L.fw0, g, rs * N3 * L.c.size(), kind(where, true), ctx->stream));
+  if (where == FLGF_HOST) CK(cudaStreamSynchronize(ctx->stream));
+  return FLGF_OK;
+}
+
+extern "C" int flgf_solve_adjoint(flgf_blockset* bs) {
+  if (!bs) return FLGF_EINVAL;
+  flgf_ctx* ctx = bs->ctx;
+  collect_times(bs);
+  bs->ev_used = 0;
+  cudaError_t e = ctx->prec == FLGF_FP64 ? enqueue_adjoint<double>(bs) : enqueue_adjoint<float>(bs);
+  if (e != cudaSuccess) return fail(ctx, FLGF_ECUDA, std::string("solve_adjoint: ") + cudaGetErrorString(e));
+  bs->ev_pending = bs->timing && bs->ev_used > 0;
+  bs->adj_solved = true;
+  return FLGF_OK;
+}
+
+extern "C" int flgf_get_gradient(flgf_blockset* bs, int problem, int level, void* out, int where) {
+  if (!bs || !out || (where != FLGF_HOST && where != FLGF_DEVICE)) return FLGF_EINVAL;
+  flgf_ctx* ctx = bs->ctx;
+  if (check_pl(bs, problem, level) != FLGF_OK) return fail(ctx, FLGF_EINVAL, "get_gradient: bad problem/level");
+  if (!bs->adj_solved) return fail(ctx, FLGF_ESTATE, "get_gradient before solve_adjoint");
+  const LevelInfo& L = bs->prob[problem].lev[level];
+  const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4, N3 = (size_t)ctx->N * ctx->N * ctx->N;
+  CK(cudaMemcpyAsync(out, (char*)bs->gf + rs * N3 * L.fw0, rs * N3 * L.c.size(), kind(where, false), ctx->stream));
+  if (where == FLGF_HOST) CK(cudaStreamSynchronize(ctx->stream));
   return FLGF_OK;
 }
 

@@ -104,6 +104,18 @@ cudaError_t launch_coarsen(int N, const R* fine_f, const int* fine_ids, R* coars
 template <typename R>
 cudaError_t launch_cf_interp(int N, const R* ucoarse, const int* nbr27, const int* fine_ids, const int* cpos,
                              int n, R* fine, int mode, const double* inv_hf2, int* err_flag, cudaStream_t s);
+// Adjoint operators: dst[i] (+)= s1[i] + s2[i] (ids < 0 contribute nothing);
+// transpose of launch_cf_interp (scatter-add onto the coarse field); transpose
+// of the coarsening (spread 1/8 to the children, zero the coarse block).
+template <typename R>
+cudaError_t launch_combine_blocks(int N, R* dst, const int* dst_ids, const R* s1, const int* s1_ids, const R* s2,
+                                  const int* s2_ids, int accumulate, int n, cudaStream_t s);
+template <typename R>
+cudaError_t launch_cf_interp_adjoint(int N, R* gcoarse, const int* nbr27, const R* gfine, const int* fine_ids,
+                                     const int* cpos, int n, int mode, const double* inv_hf2, int* err_flag,
+                                     cudaStream_t s);
+template <typename R>
+cudaError_t launch_coarsen_adjoint(int N, R* g, const int* fine_ids, const int* coarse_ids, int n, cudaStream_t s);
 // 7-point Laplacian with same-level face neighbours nbr6[i][6] (-1 absent -> 0 output).
 template <typename R>
 cudaError_t launch_laplacian(int N, const R* u, const int* nbr6, int n, double inv_h2, R* out, cudaStream_t s);

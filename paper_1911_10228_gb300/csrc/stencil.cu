@@ -265,6 +265,134 @@ __global__ void cf_interp_kernel(int N, const R* __restrict__ ucoarse, const int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint (transpose) operators for gradients.
+// ---------------------------------------------------------------------------
+
+// dst[dst_ids[i]] (+)= (s1_ids[i] >= 0 ? s1[s1_ids[i]] : 0) + (s2_ids[i] >= 0 ? s2[s2_ids[i]] : 0)
+template <typename R>
+__global__ void combine_blocks_kernel(int N, R* __restrict__ dst, const int* __restrict__ dst_ids,
+                                      const R* __restrict__ s1, const int* __restrict__ s1_ids,
+                                      const R* __restrict__ s2, const int* __restrict__ s2_ids, int accumulate) {
+  const int N3 = N * N * N;
+  const int i = blockIdx.x;
+  const int a = s1_ids[i], b = s2_ids ? s2_ids[i] : -1;
+  R* d = dst + (size_t)dst_ids[i] * N3;
+  for (int e = threadIdx.x; e < N3; e += blockDim.x) {
+    R v = R(0);
+    if (a >= 0) v += s1[(size_t)a * N3 + e];
+    if (b >= 0) v += s2[(size_t)b * N3 + e];
+    d[e] = accumulate ? d[e] + v : v;
+  }
+}
+
+// Transpose of cf_interp_kernel: the adjoint field on one fine block (mode 0),
+// or the adjoint of the correction source on it (mode 1: first the transpose
+// of the 7-point stencil onto the (N+2)^3 region, sign included), is spread
+// back through the tensor-product quadratic weights onto the coarse region of
+// the parent's 3x3x3 neighbourhood and added to the coarse field with atomics
+// (neighbouring fine blocks share coarse cells).
+template <typename R>
+__global__ void cf_interp_adjoint_kernel(int N, R* __restrict__ gcoarse, const int* __restrict__ nbr27,
+                                         const R* __restrict__ gfine, const int* __restrict__ fine_ids,
+                                         const int* __restrict__ cposv, int mode, const double* __restrict__ inv_hf2,
+                                         int* err_flag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N3 = N * N * N;
+  const int halo = mode == 1 ? 1 : 0;
+  const int F = N + 2 * halo;
+  const int M = N / 2 + 2 + 2 * halo;
+  R* C = reinterpret_cast<R*>(smem_raw);  // [M][M][M]
+  R* T1 = C + M * M * M;                  // [M][M][F]
+  R* T2 = T1 + M * M * F;                 // [M][F][F]
+  R* U = T2 + M * F * F;                  // [F][F][F]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int c = cposv[blockIdx.x];
+  const int cp[3] = {c >> 2, (c >> 1) & 1, c & 1};
+  int cbase[3];
+  for (int a = 0; a < 3; ++a) cbase[a] = ((cp[a] * N - halo) >> 1) - 1;
+  const R* g = gfine + (size_t)fine_ids[blockIdx.x] * N3;
+  if (mode == 0) {
+    for (int o = tid; o < N3; o += nt) U[o] = g[o];
+  } else {
+    const R ih2 = (R)inv_hf2[blockIdx.x];
+    for (int o = tid; o < F * F * F; o += nt) {
+      const int x[3] = {o / (F * F) - 1, (o / F) % F - 1, o % F - 1};  // fine index relative to the block
+      auto in = [&](int i, int j, int k) { return i >= 0 && i < N && j >= 0 && j < N && k >= 0 && k < N; };
+      auto gv = [&](int i, int j, int k) { return in(i, j, k) ? g[(i * N + j) * N + k] : R(0); };
+      R v = gv(x[0] + 1, x[1], x[2]) + gv(x[0] - 1, x[1], x[2]) + gv(x[0], x[1] + 1, x[2]) + gv(x[0], x[1] - 1, x[2]) +
+            gv(x[0], x[1], x[2] + 1) + gv(x[0], x[1], x[2] - 1) - R(6) * gv(x[0], x[1], x[2]);
+      U[o] = -v * ih2;  // the correction subtracts the stencil
+    }
+  }
+  __syncthreads();
+  // transpose of the axis-0 pass: T2[ci][j][k] = sum_g w U[g][j][k]
+  for (int o = tid; o < M * F * F; o += nt) {
+    const int jk = o % (F * F), ci = o / (F * F);
+    R s = 0;
+    for (int gg = 0; gg < F; ++gg) {
+      const int G = cp[0] * N + gg - halo, e = ci - ((G >> 1) - cbase[0]) + 1;
+      if (e >= 0 && e < 3) s += (R)cf_w(G & 1, e) * U[gg * F * F + jk];
+    }
+    T2[o] = s;
+  }
+  __syncthreads();
+  for (int o = tid; o < M * M * F; o += nt) {  // axis 1
+    const int k = o % F, cj = (o / F) % M, i = o / (M * F);
+    R s = 0;
+    for (int gg = 0; gg < F; ++gg) {
+      const int G = cp[1] * N + gg - halo, e = cj - ((G >> 1) - cbase[1]) + 1;
+      if (e >= 0 && e < 3) s += (R)cf_w(G & 1, e) * T2[(i * F + gg) * F + k];
+    }
+    T1[o] = s;
+  }
+  __syncthreads();
+  for (int o = tid; o < M * M * M; o += nt) {  // axis 2
+    const int ck = o % M, ij = o / M;
+    R s = 0;
+    for (int gg = 0; gg < F; ++gg) {
+      const int G = cp[2] * N + gg - halo, e = ck - ((G >> 1) - cbase[2]) + 1;
+      if (e >= 0 && e < 3) s += (R)cf_w(G & 1, e) * T1[ij * F + gg];
+    }
+    C[o] = s;
+  }
+  __syncthreads();
+  const int* nb = nbr27 + (size_t)blockIdx.x * 27;
+  for (int o = tid; o < M * M * M; o += nt) {
+    const R v = C[o];
+    const int x[3] = {o / (M * M) + cbase[0], (o / M) % M + cbase[1], o % M + cbase[2]};
+    int e[3], loc[3];
+    for (int a = 0; a < 3; ++a) {
+      e[a] = x[a] < 0 ? -1 : (x[a] >= N ? 1 : 0);
+      loc[a] = x[a] - e[a] * N;
+    }
+    const int b = nb[(e[0] + 1) * 9 + (e[1] + 1) * 3 + (e[2] + 1)];
+    if (b >= 0) {
+      atomicAdd(&gcoarse[(size_t)b * N3 + (loc[0] * N + loc[1]) * N + loc[2]], v);
+    } else if (v != R(0) && err_flag) {
+      atomicExch(err_flag, 1);
+    }
+  }
+}
+
+// Transpose of the coarsening: every cell of the 8 children receives 1/8 of
+// its coarse cell's adjoint, and the coarse (non-leaf) block is zeroed (its
+// forward value was overwritten, so the user's value has zero gradient).
+template <typename R>
+__global__ void coarsen_adjoint_kernel(int N, R* __restrict__ g, const int* __restrict__ fine_ids,
+                                       const int* __restrict__ coarse_ids) {
+  const int N3 = N * N * N, H = N / 2;
+  R* gc = g + (size_t)coarse_ids[blockIdx.x] * N3;
+  for (int o = threadIdx.x; o < 8 * N3; o += blockDim.x) {
+    const int a = o / N3, r = o % N3;
+    const int i = r / (N * N), j = (r / N) % N, k = r % N;
+    const int ci = (a >> 2) * H + i / 2, cj = ((a >> 1) & 1) * H + j / 2, ck = (a & 1) * H + k / 2;
+    g[(size_t)fine_ids[blockIdx.x * 8 + a] * N3 + r] += R(0.125) * gc[(ci * N + cj) * N + ck];
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < N3; o += blockDim.x) gc[o] = R(0);
+}
+
 template <typename R>
 __global__ void laplacian_kernel(int N, const R* __restrict__ u, const int* __restrict__ nbr6, double inv_h2,
                                  R* __restrict__ out) {
@@ -387,6 +515,36 @@ cudaError_t launch_cf_interp(int N, const R* ucoarse, const int* nbr27, const in
 }
 
 template <typename R>
+cudaError_t launch_combine_blocks(int N, R* dst, const int* dst_ids, const R* s1, const int* s1_ids, const R* s2,
+                                  const int* s2_ids, int accumulate, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  combine_blocks_kernel<R><<<n, threads_for(N), 0, s>>>(N, dst, dst_ids, s1, s1_ids, s2, s2_ids, accumulate);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_cf_interp_adjoint(int N, R* gcoarse, const int* nbr27, const R* gfine, const int* fine_ids,
+                                     const int* cpos, int n, int mode, const double* inv_hf2, int* err_flag,
+                                     cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int halo = mode == 1 ? 1 : 0;
+  const int F = N + 2 * halo, M = N / 2 + 2 + 2 * halo;
+  const size_t sm = sizeof(R) * ((size_t)M * M * M + M * M * F + M * F * F + F * F * F);
+  cudaError_t e = set_smem(cf_interp_adjoint_kernel<R>, sm);
+  if (e != cudaSuccess) return e;
+  cf_interp_adjoint_kernel<R><<<n, threads_for(N), sm, s>>>(N, gcoarse, nbr27, gfine, fine_ids, cpos, mode, inv_hf2,
+                                                            err_flag);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_coarsen_adjoint(int N, R* g, const int* fine_ids, const int* coarse_ids, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  coarsen_adjoint_kernel<R><<<n, threads_for(N), 0, s>>>(N, g, fine_ids, coarse_ids);
+  return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_laplacian(int N, const R* u, const int* nbr6, int n, double inv_h2, R* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   laplacian_kernel<R><<<n, threads_for(N), 0, s>>>(N, u, nbr6, inv_h2, out);
@@ -402,7 +560,12 @@ cudaError_t launch_laplacian(int N, const R* u, const int* nbr6, int n, double i
   template cudaError_t launch_coarsen<R>(int, const R*, const int*, R*, const int*, int, cudaStream_t);         \
   template cudaError_t launch_cf_interp<R>(int, const R*, const int*, const int*, const int*, int, R*, int,     \
                                            const double*, int*, cudaStream_t);                                        \
-  template cudaError_t launch_laplacian<R>(int, const R*, const int*, int, double, R*, cudaStream_t);
+  template cudaError_t launch_laplacian<R>(int, const R*, const int*, int, double, R*, cudaStream_t);            \
+  template cudaError_t launch_combine_blocks<R>(int, R*, const int*, const R*, const int*, const R*, const int*, \
+                                                int, int, cudaStream_t);                                        \
+  template cudaError_t launch_cf_interp_adjoint<R>(int, R*, const int*, const R*, const int*, const int*, int,  \
+                                                   int, const double*, int*, cudaStream_t);                     \
+  template cudaError_t launch_coarsen_adjoint<R>(int, R*, const int*, const int*, int, cudaStream_t);
 FLGF_INST(float)
 FLGF_INST(double)
 

@@ -63,6 +63,9 @@ PROTOTYPES = {
     "flgf_stage_times": (ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, ctypes.c_int, _c_int_p, ctypes.c_int]),
     "flgf_work_counts": (ctypes.c_int, [ctypes.c_void_p, _c_i64_p, _c_i64_p, _c_i64_p, _c_i64_p]),
     "flgf_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "flgf_load_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    "flgf_solve_adjoint": (ctypes.c_int, [ctypes.c_void_p]),
+    "flgf_get_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
     "flgf_convolve_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_i32_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_double]),
 }
@@ -246,6 +249,32 @@ class BlockSet:
                                                    FLGF_DEVICE), "flgf_get_potential")
         torch.cuda.current_stream(self.ctx.device).wait_stream(self.ctx.stream)
         return out
+
+    def load_adjoint(self, problem: int, level: int, g):
+        """Adjoint seed dL/du of (problem, level), shape (nblk, N, N, N)."""
+        shape = self._shape(problem, level)
+        t = torch.as_tensor(g).to(device=self.ctx.device, dtype=self.ctx.dtype).contiguous()
+        if tuple(t.shape) != shape:
+            raise ValueError(f"adjoint shape {tuple(t.shape)} != {shape}")
+        self.ctx.stream.wait_stream(torch.cuda.current_stream(self.ctx.device))
+        self.ctx.check(self.lib.flgf_load_adjoint(self.handle, problem, level, ctypes.c_void_p(t.data_ptr()),
+                                                  FLGF_DEVICE), "flgf_load_adjoint")
+        t.record_stream(self.ctx.stream)
+
+    def solve_adjoint(self):
+        self.ctx.check(self.lib.flgf_solve_adjoint(self.handle), "flgf_solve_adjoint")
+
+    def gradient(self, problem: int = 0, level: int = 0) -> torch.Tensor:
+        """dL/df of (problem, level) after solve_adjoint, as a device tensor."""
+        out = torch.empty(self._shape(problem, level), dtype=self.ctx.dtype, device=self.ctx.device)
+        self.ctx.stream.wait_stream(torch.cuda.current_stream(self.ctx.device))
+        self.ctx.check(self.lib.flgf_get_gradient(self.handle, problem, level, ctypes.c_void_p(out.data_ptr()),
+                                                  FLGF_DEVICE), "flgf_get_gradient")
+        torch.cuda.current_stream(self.ctx.device).wait_stream(self.ctx.stream)
+        return out
+
+    def keys(self):
+        return [(p, l) for p in range(len(self.levels)) for l in range(len(self.levels[p]))]
 
     def potential_host(self, problem: int = 0, level: int = 0, out: np.ndarray | None = None) -> np.ndarray:
         """u into host memory (``out``: e.g. a pinned buffer of the right shape and dtype)."""
