@@ -147,7 +147,8 @@ int flgf_laplacian(flgf_blockset* bs, int problem, int level, const void* u, voi
  * accumulation, selection and coarsening steps in reverse order, and the FMMs
  * (symmetric: R = J^T and G(n) = G(-n)), the leaf-only one with its source
  * and target sets swapped.  The gradient of a loss with dL/du = g is then
- * dL/df = A^T g, zero on non-leaf blocks.  Seeds persist until reloaded.
+ * dL/df = A^T g, zero on non-leaf blocks.  Seeds persist until reloaded; the
+ * potentials of the last flgf_solve stay valid.
  * Enqueued on the context stream; the source correction option applies. */
 int flgf_load_adjoint(flgf_blockset* bs, int problem, int level, const void* g, int where);
 int flgf_solve_adjoint(flgf_blockset* bs);

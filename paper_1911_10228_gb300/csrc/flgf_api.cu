@@ -173,6 +173,7 @@ struct flgf_blockset {
   void* gW = nullptr;      // adjoint of W, [B][N^3]
   void* gf = nullptr;      // adjoint of the level sources -> the gradient, [B][N^3]
   void* gtmp = nullptr;    // [B][N^3]
+  void* aunodes = nullptr; // FMM outputs of the adjoint, [G][N^3] (the potentials stay in unodes)
   bool adj_solved = false;
   void* spec = nullptr;
   void* acc = nullptr;
@@ -382,6 +383,7 @@ extern "C" void flgf_blockset_destroy(flgf_blockset* bs) {
   cudaFree(bs->gW);
   cudaFree(bs->gf);
   cudaFree(bs->gtmp);
+  cudaFree(bs->aunodes);
   cudaFree(bs->spec);
   cudaFree(bs->acc);
   cudaFree(bs->lap_in);
@@ -934,6 +936,7 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
   if (e == cudaSuccess) e = alloc(&bs->gW, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->gf, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->gtmp, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = alloc(&bs->aunodes, rs * N3 * bs->G);
   if (e == cudaSuccess) e = cudaMemset(bs->gseed, 0, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->spec, 2 * rs * NW * bs->max_phase_blocks);
   if (e == cudaSuccess) e = alloc(&bs->acc, 2 * rs * NW * bs->max_phase_blocks);
@@ -1025,14 +1028,15 @@ struct StageScope {
   }
 };
 
+// FMM of one phase: upward pass over `nodes`, forward FFTs, spectrum MAC,
+// inverse FFTs and downward pass into `unodes`.
 template <typename R>
-cudaError_t enqueue_fmm(flgf_blockset* bs, const PhaseOff& ph) {
+cudaError_t enqueue_fmm(flgf_blockset* bs, const PhaseOff& ph, R* unodes) {
   flgf_ctx* c = bs->ctx;
   const int N = c->N;
   cudaStream_t s = c->stream;
   const Arena& ar = bs->ar;
   R* nodes = (R*)bs->nodes;
-  R* unodes = (R*)bs->unodes;
   cudaError_t e;
 #define KRUN(n, x)                              \
   do {                                          \
@@ -1083,7 +1087,7 @@ cudaError_t enqueue_adjoint(flgf_blockset* bs) {
   const Arena& ar = bs->ar;
   const size_t N3 = (size_t)N * N * N;
   R* nodes = (R*)bs->nodes;
-  R* unodes = (R*)bs->unodes;
+  R* unodes = (R*)bs->aunodes;
   R* gseed = (R*)bs->gseed;
   R* gW = (R*)bs->gW;
   R* gf = (R*)bs->gf;
@@ -1110,7 +1114,7 @@ cudaError_t enqueue_adjoint(flgf_blockset* bs) {
       KRUN(ao.n_prep, launch_combine_blocks<R>(N, nodes, ar.at<int>(ao.prep_dst), gseed, ar.at<int>(ao.prep_s1), gW,
                                                ar.at<int>(ao.prep_s2), 0, ao.n_prep, s));
     }
-    if ((e = enqueue_fmm<R>(bs, bs->aph[l])) != cudaSuccess) return e;
+    if ((e = enqueue_fmm<R>(bs, bs->aph[l], unodes)) != cudaSuccess) return e;
     {
       StageScope sc(bs, 6);
       KRUN(ao.n_gacc, launch_combine_blocks<R>(N, gf, ar.at<int>(ao.gacc_dst), unodes, ar.at<int>(ao.gacc_s1), unodes,
@@ -1168,7 +1172,7 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
       KRUN(ph.n_prep, launch_copy_blocks<R>(N, fwork, ar.at<int>(ph.prep_src), nodes, ar.at<int>(ph.prep_dst),
                                             ar.at<uint8_t>(ph.prep_zero), ph.n_prep, s));
     }
-    if ((e = enqueue_fmm<R>(bs, ph)) != cudaSuccess) return e;
+    if ((e = enqueue_fmm<R>(bs, ph, unodes)) != cudaSuccess) return e;
     {
       StageScope sc(bs, 6);
       R* wf = (R*)bs->wfield;

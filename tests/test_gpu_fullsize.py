@@ -90,7 +90,10 @@ def test_torus_multires_laplacian_consistency_and_fp32():
     for l in range(p.n_levels):
         a = u32[l].double().cpu().numpy()[leaf[l]]
         b = u64[l].cpu().numpy()[leaf[l]]
-        assert rel(a, b) < 1e-5, l
+        err = rel(a, b)
+        print(f"torus level {l}: FP32 vs FP64 rel err {err:.3e}")
+        # FP32 with the source correction (a 1/h^2-scaled stencil of FP32 fields): 1e-4
+        assert err < 1e-4, (l, err)
     bs.close()
     c64.close()
     c32.close()
