@@ -52,6 +52,7 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precisions", default="fp32,fp64", help="contexts to time (profiling runs use fp32)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched leg")
     return ap.parse_args()
 
 
@@ -254,6 +255,54 @@ def run_ours(a, rank, world, dist):
         }
         res[prec]["u"] = bs.potential(0, 0).double().cpu().numpy()
 
+    # batched form: 64 independent refined problems in one block set, every stage
+    # of all problems in the same launches, the whole solve replayed as a CUDA graph
+    batched = None
+    if not a.no_batched:
+        from paper_1911_10228_gb300.inputs import config_batched
+        probs = config_batched()
+        bdof = sum(p.dof() for p in probs)
+        batched = {"workload": "64 random sparse problems (seeds 0-63), 16^3 blocks, block counts log-uniform "
+                               "in [8, 4096] over 1-3 levels, 1-4 Gaussians each, one block set, CUDA graph",
+                   "dof": bdof, "blocks": int(sum(len(c) for p in probs for c in p.coords))}
+        outs = {}
+        for prec in precs:
+            bctx = F.Context(N=16, n_interp=6, precision=prec)
+            bbs = F.BlockSet(bctx, [p.coords for p in probs], [p.h0 for p in probs])
+            for i, p in enumerate(probs):
+                for l, f in enumerate(p.f):
+                    bbs.load_source(i, l, torch.as_tensor(f))
+            bbs.set_option(F.OPT_GRAPH, 1)
+            for _ in range(max(1, a.warmup)):
+                bbs.solve()
+            torch.cuda.synchronize()
+            nb = a.steps if prec == "fp32" else max(2, min(a.steps, 4))
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb)]
+            sampler.start()
+            for s0, s1 in ev:
+                with torch.cuda.stream(bctx.stream):
+                    flush.zero_()
+                s0.record(bctx.stream)
+                bbs.solve()
+                s1.record(bctx.stream)
+            torch.cuda.synchronize()
+            sampler.stop()
+            ms = float(np.mean([s0.elapsed_time(s1) for s0, s1 in ev]))
+            batched[prec] = {"value": bdof * world / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "steps": nb,
+                             "launches_per_step": bbs.launch_count()}
+            outs[prec] = [[bbs.potential(i, l) for l in range(p.n_levels)] for i, p in enumerate(probs)]
+            bbs.close()
+            bctx.close()
+        if "fp64" in outs:   # FP32 batched form against the FP64 solve, leaf cells, max over all problems
+            num, den = 0.0, 0.0
+            for u32s, u64s, p in zip(outs["fp32"], outs["fp64"], probs):
+                for x32, x64, lm in zip(u32s, u64s, p.leaf_masks()):
+                    m = torch.as_tensor(lm, device=x64.device)
+                    num = max(num, float((x32.double() - x64)[m].abs().max()))
+                    den = max(den, float(x64[m].abs().max()))
+            batched["fp32_vs_fp64_linf"] = num / den
+        del outs
+
     # end-to-end FP32 through the public API with pinned host buffers
     r32 = res["fp32"]
     bs = r32["bs"]
@@ -344,6 +393,7 @@ def run_ours(a, rank, world, dist):
                         "fft_inverse_gbs": rows["fp32"]["fft_inv_gbs"],
                         "fft_inverse_frac": rows["fp32"]["fft_inv_gbs"] / hbm},
         "stages_ms": res["fp32"]["stages_ms"],
+        "batched": batched,
         "cpu_baseline": cpu,
         "e2e": None if e2e_ms_step is None else {
             "value": dof * world / (e2e_ms_step / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": nbytes,

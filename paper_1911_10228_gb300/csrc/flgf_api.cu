@@ -637,27 +637,33 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
                     const int qq = ((x >> 1) * tl.Rg[1] + (y >> 1)) * tl.Rg[2] + (z >> 1);
                     sg[b * NQ + qq] = i >= 0 && in.is_src[k][i] ? in.gid0[k] + i - ph.gid_begin : -1;
                   }
-              // count interacting (target, source) pairs for the work accounting
-              for (int x = 0; x < 2 * tl.P[0]; ++x)
-                for (int y = 0; y < 2 * tl.P[1]; ++y)
-                  for (int z = 0; z < 2 * tl.P[2]; ++z) {
-                    if (tg[(x * 2 * tl.P[1] + y) * 2 * tl.P[2] + z] < 0) continue;
-                    const int tc[3] = {2 * t0 + x, 2 * t1 + y, 2 * t2 + z};
-                    for (int sx = 0; sx < 2 * tl.Rg[0]; ++sx)
-                      for (int sy = 0; sy < 2 * tl.Rg[1]; ++sy)
-                        for (int sz = 0; sz < 2 * tl.Rg[2]; ++sz) {
-                          const int b = ((sx & 1) << 2) | ((sy & 1) << 1) | (sz & 1);
-                          const int qq = ((sx >> 1) * tl.Rg[1] + (sy >> 1)) * tl.Rg[2] + (sz >> 1);
-                          if (sg[b * NQ + qq] < 0) continue;
-                          const int sc[3] = {2 * tl.r0[0] + sx, 2 * tl.r0[1] + sy, 2 * tl.r0[2] + sz};
-                          bool inlist = true, near = true;
+              // count interacting (target, source) pairs for the work accounting:
+              // a target's candidates are the children of its parent's 27 neighbours
+              if (count) {
+                for (int x = 0; x < 2 * tl.P[0]; ++x)
+                  for (int y = 0; y < 2 * tl.P[1]; ++y)
+                    for (int z = 0; z < 2 * tl.P[2]; ++z) {
+                      if (tg[(x * 2 * tl.P[1] + y) * 2 * tl.P[2] + z] < 0) continue;
+                      const int tc[3] = {2 * t0 + x, 2 * t1 + y, 2 * t2 + z};
+                      for (int e = 0; e < 27; ++e)
+                        for (int b = 0; b < 8; ++b) {
+                          const int sc[3] = {2 * ((tc[0] >> 1) + e / 9 - 1) + (b >> 2),
+                                             2 * ((tc[1] >> 1) + (e / 3) % 3 - 1) + ((b >> 1) & 1),
+                                             2 * ((tc[2] >> 1) + e % 3 - 1) + (b & 1)};
+                          int rr[3];
+                          bool in = true, near = true;
                           for (int a = 0; a < 3; ++a) {
-                            if (std::abs((sc[a] >> 1) - (tc[a] >> 1)) > 1) inlist = false;
-                            if (std::abs(sc[a] - tc[a]) > 1) near = false;
+                            rr[a] = sc[a] - 2 * tl.r0[a];
+                            in &= rr[a] >= 0 && rr[a] < 2 * tl.Rg[a];
+                            near &= std::abs(sc[a] - tc[a]) <= 1;
                           }
-                          if (count && inlist && !(excl && near)) bs->pairs++;
+                          if (!in || (excl && near)) continue;
+                          const int bb = ((rr[0] & 1) << 2) | ((rr[1] & 1) << 1) | (rr[2] & 1);
+                          const int qq = ((rr[0] >> 1) * tl.Rg[1] + (rr[1] >> 1)) * tl.Rg[2] + (rr[2] >> 1);
+                          if (sg[bb * NQ + qq] >= 0) bs->pairs++;
                         }
-                  }
+                    }
+              }
               // threads: (parent slot, frequency group, chunk); small tiles take
               // several chunks per CTA, bounded by shared memory (~100 KB)
               const int np = tl.P[0] * tl.P[1] * tl.P[2];

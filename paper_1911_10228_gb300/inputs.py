@@ -242,17 +242,32 @@ def smooth_field(x, seed: int = 1, n_modes: int = 4):
     return out / n_modes
 
 
+def gaussians_separable(coords, N: int, h: float, centres, sigmas, amps) -> np.ndarray:
+    """Sum of Gaussians on the cells of a block set, each evaluated as the product
+    of its three 1-D factors per block (same values as ``gaussians``)."""
+    coords = np.asarray(coords, dtype=np.int64)
+    out = np.zeros((len(coords), N, N, N))
+    ax = np.arange(N)
+    for c, s, a in zip(centres, sigmas, amps):
+        e = [np.exp(-(((coords[:, d, None] * N + ax[None, :]) + 0.5) * h - c[d]) ** 2 / (2.0 * s * s))
+             for d in range(3)]
+        out += a * np.einsum("bi,bj,bk->bijk", e[0], e[1], e[2], optimize=True)
+    return out
+
+
 def random_sparse_problem(seed: int, N: int = 16, nblk_range=(8, 4096), max_levels: int = 3) -> Problem:
     """Random disjoint sparse block set with 1..max_levels levels and 1-4 Gaussians.
 
-    Total block count ~ round(exp U[ln a, ln b]) over levels; base blocks are a
-    random subset of a cube of side ceil((4 nblk_base)^(1/3)); about 25 % of the
-    blocks of each level are refined (closed with the neighbour buffer).
+    Total block count over levels ~ round(exp U[ln a, ln b]).  The base level is a
+    random subset of a cube of side ceil((4 nblk_base)^(1/3)); on every level the
+    quarter of the blocks nearest to a random centre is refined (closed with the
+    26-neighbour buffer), so each refinement roughly doubles the block count and
+    the base holds about 1/(1 + 2 + 4) of the blocks for three levels.
     """
     rng = np.random.default_rng(seed)
     n_target = int(round(math.exp(rng.uniform(math.log(nblk_range[0]), math.log(nblk_range[1])))))
     L = int(rng.integers(1, max_levels + 1))
-    n_base = max(1, int(round(n_target / (1.0 + 0.25 * 8 * (L - 1)))))
+    n_base = max(1, int(round(n_target / sum(2 ** l for l in range(L)))))
     side = max(2, int(math.ceil((4 * n_base) ** (1.0 / 3.0))))
     allc = box_coords(side)
     pick = rng.choice(len(allc), size=min(n_base, len(allc)), replace=False)
@@ -262,14 +277,15 @@ def random_sparse_problem(seed: int, N: int = 16, nblk_range=(8, 4096), max_leve
     cen = rng.uniform(0.25, 0.75, (ng, 3))
     sig = rng.uniform(0.03, 0.1, ng)
     amp = rng.uniform(-1, 1, ng)
-    src = lambda x: gaussians(x, cen, sig, amp)
+    focus = rng.uniform(0.3, 0.7, 3)
     levels = [set(map(tuple, base.tolist()))]
     refined = [set() for _ in range(L)]
     for l in range(L - 1):
-        cl = sorted(levels[l])
+        cl = np.array(sorted(levels[l]), dtype=np.int64)
         k = max(1, int(round(0.25 * len(cl))))
-        sel = rng.choice(len(cl), size=k, replace=False)
-        refined[l] = {cl[i] for i in sel}
+        centre = focus * side * (1 << l)
+        near = np.argsort(np.sum((cl + 0.5 - centre) ** 2, axis=1), kind="stable")[:k]
+        refined[l] = {tuple(v) for v in cl[near].tolist()}
         changed = True
         while changed:
             changed = False
@@ -284,7 +300,13 @@ def random_sparse_problem(seed: int, N: int = 16, nblk_range=(8, 4096), max_leve
     p = Problem(N=N, h0=h0, name=f"rand{seed}")
     for l in range(L):
         p.coords.append(np.array(sorted(levels[l]), dtype=np.int64).reshape(-1, 3))
-    ref = max(np.max(np.abs(src(cell_centres(c, N, h0 / (1 << l))))) for l, c in enumerate(p.coords))
-    for l, cl in enumerate(p.coords):
-        p.f.append(truncate(src(cell_centres(cl, N, h0 / (1 << l))), ref))
+    vals = [gaussians_separable(c, N, h0 / (1 << l), cen, sig, amp) for l, c in enumerate(p.coords)]
+    ref = max(np.max(np.abs(v)) for v in vals)
+    p.f = [truncate(v, ref) for v in vals]
     return p
+
+
+def config_batched(n_problems: int = 64, N: int = 16):
+    """64 independent problems (seeds 0..63): block counts log-uniform in [8, 4096]
+    over 1-3 levels, random disjoint sparse base sets, random Gaussian sources."""
+    return [random_sparse_problem(s, N=N) for s in range(n_problems)]
