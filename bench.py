@@ -273,10 +273,11 @@ def run_ours(a, rank, world, dist):
                 for l, f in enumerate(p.f):
                     bbs.load_source(i, l, torch.as_tensor(f))
             bbs.set_option(F.OPT_GRAPH, 1)
-            for _ in range(max(1, a.warmup)):
+            # the FP64 batched solve takes seconds: one warm-up and one step (it serves the error check)
+            for _ in range(max(1, a.warmup) if prec == "fp32" else 1):
                 bbs.solve()
             torch.cuda.synchronize()
-            nb = a.steps if prec == "fp32" else max(2, min(a.steps, 4))
+            nb = a.steps if prec == "fp32" else 1
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb)]
             sampler.start()
             for s0, s1 in ev:
