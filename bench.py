@@ -266,8 +266,19 @@ def run_ours(a, rank, world, dist):
                                "in [8, 4096] over 1-3 levels, 1-4 Gaussians each, one block set, CUDA graph",
                    "dof": bdof, "blocks": int(sum(len(c) for p in probs for c in p.coords))}
         outs = {}
+        plan = None
         for prec in precs:
             bctx = F.Context(N=16, n_interp=6, precision=prec)
+            if plan is None:
+                # pick the MAC plan (dense tile, pair-list threshold) on this mesh
+                from paper_1911_10228_gb300.autotune import autotune
+                t0 = time.time()
+                plan, table = autotune(bctx, [p.coords for p in probs], [p.h0 for p in probs], reps=2)
+                batched["autotune"] = {"precision": prec, "plan": {"list_pct": plan[0], "tile": list(plan[1])},
+                                       "seconds": round(time.time() - t0, 1),
+                                       "ms_per_solve": {f"{k[0]}/{'x'.join(map(str, k[1]))}": round(v, 2)
+                                                        for k, v in table.items()}}
+            bctx.set_plan(list_pct=plan[0], tile=plan[1])
             bbs = F.BlockSet(bctx, [p.coords for p in probs], [p.h0 for p in probs])
             for i, p in enumerate(probs):
                 for l, f in enumerate(p.f):

@@ -89,6 +89,22 @@ void flgf_default_opts(flgf_opts* o);
  * G(2^k (N d + Delta))).  Synchronises the stream.  *out is NULL on failure. */
 int flgf_create(flgf_ctx** out, const flgf_opts* o);
 void flgf_destroy(flgf_ctx* ctx);
+/* Plan options of a context: they shape the launch lists of block sets
+ * created afterwards (existing block sets keep theirs).  The paper has no
+ * counterpart; they exist for tuning the spectrum multiply-accumulate:
+ *   FLGF_CTX_LIST_PCT  0..100 (default 30): an interaction tile whose useful
+ *                      (target, source) pairs are below this percentage of the
+ *                      work of the dense parent-group kernel (8 x 8 children of
+ *                      every neighbour parent pair, absent blocks included)
+ *                      runs on the pair-list kernel instead; 0 = never.
+ *   FLGF_CTX_TILE      dense tile in parents, t0 | t1 << 8 | t2 << 16 with
+ *                      1 <= t_a <= 8, t0 t1 t2 <= 128 and
+ *                      (t0 + 2)(t1 + 2)(t2 + 2) <= 397 (the tile's source
+ *                      region must fit shared memory); default 4 x 4 x 8.
+ * FLGF_EINVAL for an unknown key or a value out of range. */
+enum { FLGF_CTX_LIST_PCT = 1, FLGF_CTX_TILE = 2 };
+int flgf_ctx_set_option(flgf_ctx* ctx, int key, int value);
+
 /* Message of the last failure on this context (never NULL; "" if none). */
 const char* flgf_last_error(const flgf_ctx* ctx);
 

@@ -17,6 +17,9 @@ using namespace flgf;
 
 struct flgf_ctx {
   int N = 16, nI = 6, prec = FLGF_FP64, max_oct = 6, R = 100, RA = 600;
+  // plan options for block sets created afterwards (flgf_ctx_set_option)
+  int list_pct = 30;             // pair-list MAC below this useful fraction of the dense kernel's work
+  int tile[3] = {4, 4, 8};       // dense MAC tile in parents
   cudaStream_t stream = nullptr;
   std::string err;
   double* d_table = nullptr;
@@ -131,6 +134,7 @@ struct PhaseOff {  // arena offsets and counts of one phase's launch lists
   std::vector<int> n_ant; std::vector<size_t> ant_par, ant_ch;
   int n_fwd = 0; size_t fwd_gid = 0, fwd_sid = 0;
   int n_tiles = 0, n_work = 0, max_cells_cpc = 0; size_t tiles = 0, work = 0, src_ids = 0, tgt_ids = 0, pmap = 0;
+  int n_groups = 0, max_group_src = 0; size_t groups = 0, l_tgt = 0, l_len = 0, l_ent = 0, l_src = 0;
   int n_inv = 0; size_t inv_sid = 0, inv_gid = 0, inv_scale = 0;
   std::vector<int> n_itp; std::vector<size_t> itp_ch, itp_par, itp_cpos;
   int n_sel = 0; size_t sel_src = 0, sel_dst = 0;
@@ -532,9 +536,12 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     ph.nblocks = bs->G - ph.gid_begin;
     bs->max_phase_blocks = std::max(bs->max_phase_blocks, ph.nblocks);
   }
+  // pair-list entries hold a phase-local block id in 22 bits
+  if (bs->max_phase_blocks >= (1 << 22))
+    return bail(FLGF_EINVAL, "more than 2^22 octree blocks in one refinement level");
   // ---- launch lists ----------------------------------------------------------
   Arena& ar = bs->ar;
-  const int TP[3] = {4, 4, 8};  // tile size in parents (<= 128 parents: 256 threads, two CTAs per SM)
+  const int TP[3] = {ctx->tile[0], ctx->tile[1], ctx->tile[2]};  // tile in parents (<= 128: 256 threads)
   // FMM launch lists of phase l for the given instances (their is_src /
   // need_tgt masks select sources and targets)
   auto build_fmm = [&](int l, const std::vector<const Inst*>& insts, PhaseOff& ph, bool count) {
@@ -550,6 +557,11 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     std::vector<HadWork> work;
     std::vector<int> src_ids, tgt_ids;
     std::vector<int2> pmap;
+    std::vector<ListGroup> groups;
+    std::vector<int> l_tgt, l_len, l_ent, l_src;
+    int max_group_src = 0;
+    // targets of sparse tiles per octree level, in tile order: (target id, pair list)
+    std::vector<std::vector<std::pair<int, std::vector<int>>>> lpool;
     const int nchunk = ctx->prec == FLGF_FP64 ? nchunks<double>(N) : nchunks<float>(N);
     for (const Inst* inp : insts) {
       const Inst& in = *inp;
@@ -637,32 +649,48 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
                     const int qq = ((x >> 1) * tl.Rg[1] + (y >> 1)) * tl.Rg[2] + (z >> 1);
                     sg[b * NQ + qq] = i >= 0 && in.is_src[k][i] ? in.gid0[k] + i - ph.gid_begin : -1;
                   }
-              // count interacting (target, source) pairs for the work accounting:
-              // a target's candidates are the children of its parent's 27 neighbours
-              if (count) {
-                for (int x = 0; x < 2 * tl.P[0]; ++x)
-                  for (int y = 0; y < 2 * tl.P[1]; ++y)
-                    for (int z = 0; z < 2 * tl.P[2]; ++z) {
-                      if (tg[(x * 2 * tl.P[1] + y) * 2 * tl.P[2] + z] < 0) continue;
-                      const int tc[3] = {2 * t0 + x, 2 * t1 + y, 2 * t2 + z};
-                      for (int e = 0; e < 27; ++e)
-                        for (int b = 0; b < 8; ++b) {
-                          const int sc[3] = {2 * ((tc[0] >> 1) + e / 9 - 1) + (b >> 2),
-                                             2 * ((tc[1] >> 1) + (e / 3) % 3 - 1) + ((b >> 1) & 1),
-                                             2 * ((tc[2] >> 1) + e % 3 - 1) + (b & 1)};
-                          int rr[3];
-                          bool in = true, near = true;
-                          for (int a = 0; a < 3; ++a) {
-                            rr[a] = sc[a] - 2 * tl.r0[a];
-                            in &= rr[a] >= 0 && rr[a] < 2 * tl.Rg[a];
-                            near &= std::abs(sc[a] - tc[a]) <= 1;
-                          }
-                          if (!in || (excl && near)) continue;
-                          const int bb = ((rr[0] & 1) << 2) | ((rr[1] & 1) << 1) | (rr[2] & 1);
-                          const int qq = ((rr[0] >> 1) * tl.Rg[1] + (rr[1] >> 1)) * tl.Rg[2] + (rr[2] >> 1);
-                          if (sg[bb * NQ + qq] >= 0) bs->pairs++;
+              // the interacting (target, source) pairs of every target: the
+              // candidates are the children of its parent's 27 neighbours
+              std::vector<std::vector<int>> plist(tg.size());  // (source id << 9) | offset index
+              int64_t useful = 0;
+              for (int x = 0; x < 2 * tl.P[0]; ++x)
+                for (int y = 0; y < 2 * tl.P[1]; ++y)
+                  for (int z = 0; z < 2 * tl.P[2]; ++z) {
+                    const int ti = (x * 2 * tl.P[1] + y) * 2 * tl.P[2] + z;
+                    if (tg[ti] < 0) continue;
+                    const int tc[3] = {2 * t0 + x, 2 * t1 + y, 2 * t2 + z};
+                    for (int e = 0; e < 27; ++e)
+                      for (int b = 0; b < 8; ++b) {
+                        const int sc[3] = {2 * ((tc[0] >> 1) + e / 9 - 1) + (b >> 2),
+                                           2 * ((tc[1] >> 1) + (e / 3) % 3 - 1) + ((b >> 1) & 1),
+                                           2 * ((tc[2] >> 1) + e % 3 - 1) + (b & 1)};
+                        int rr[3];
+                        bool in = true, near = true;
+                        for (int a = 0; a < 3; ++a) {
+                          rr[a] = sc[a] - 2 * tl.r0[a];
+                          in &= rr[a] >= 0 && rr[a] < 2 * tl.Rg[a];
+                          near &= std::abs(sc[a] - tc[a]) <= 1;
                         }
-                    }
+                        if (!in || (excl && near)) continue;
+                        const int bb = ((rr[0] & 1) << 2) | ((rr[1] & 1) << 1) | (rr[2] & 1);
+                        const int qq = ((rr[0] >> 1) * tl.Rg[1] + (rr[1] >> 1)) * tl.Rg[2] + (rr[2] >> 1);
+                        const int sid = sg[bb * NQ + qq];
+                        if (sid < 0) continue;
+                        plist[ti].push_back((sid << 9) | off_index(tc[0] - sc[0], tc[1] - sc[1], tc[2] - sc[2]));
+                      }
+                    useful += (int64_t)plist[ti].size();
+                  }
+              if (count) bs->pairs += useful;
+              std::vector<int2> tpm;
+              build_parent_map(tl, sg.data(), tg.data(), tpm);
+              int64_t dense = 0;  // complex MACs per frequency of the parent-group kernel
+              for (const int2& m : tpm) dense += 64 * (int64_t)__builtin_popcount((unsigned)m.y);
+              if (useful * 100 < (int64_t)ctx->list_pct * dense) {
+                // sparse tile: its targets join the pair-list pool of octree level k
+                if ((int)lpool.size() <= (int)k) lpool.resize(k + 1);
+                for (int ti = 0; ti < (int)tg.size(); ++ti)
+                  if (tg[ti] >= 0) lpool[k].push_back({tg[ti], std::move(plist[ti])});
+                continue;
               }
               // threads: (parent slot, frequency group, chunk); small tiles take
               // several chunks per CTA, bounded by shared memory (~100 KB)
@@ -680,9 +708,54 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
               tl.src_off = (int)src_ids.size();
               src_ids.insert(src_ids.end(), sg.begin(), sg.end());
               tl.pmap_off = (int)pmap.size();
-              build_parent_map(tl, sg.data(), pmap);
+              pmap.insert(pmap.end(), tpm.begin(), tpm.end());
               tiles.push_back(tl);
             }
+      }
+    }
+    // pair-list groups: consecutive pool targets (spatially close, so their
+    // source sets overlap) up to kListTargets targets or kListMaxSrc sources
+    for (int k = 0; k < (int)lpool.size(); ++k) {
+      const auto& pool = lpool[k];
+      size_t pos = 0;
+      while (pos < pool.size()) {
+        std::unordered_map<int, int> slot;
+        std::vector<int> gsrc, members;
+        while (pos < pool.size() && (int)members.size() < kListTargets) {
+          const auto& pl = pool[pos].second;
+          int add = 0;
+          for (int w : pl) add += slot.count(w >> 9) ? 0 : 1;
+          if (!members.empty() && (int)gsrc.size() + add > kListMaxSrc) break;
+          for (int w : pl)
+            if (!slot.count(w >> 9)) {
+              slot.emplace(w >> 9, (int)gsrc.size());
+              gsrc.push_back(w >> 9);
+            }
+          members.push_back((int)pos++);
+        }
+        // longest lists first: the threads of a warp run similar trip counts
+        std::stable_sort(members.begin(), members.end(),
+                         [&](int a, int b) { return pool[a].second.size() > pool[b].second.size(); });
+        ListGroup g;
+        g.level = k;
+        g.ntgt = (int)members.size();
+        g.maxlen = (int)pool[members[0]].second.size();
+        g.tgt_off = (int)l_tgt.size();
+        g.len_off = (int)l_len.size();
+        g.ent_off = (int)l_ent.size();
+        g.src_off = (int)l_src.size();
+        g.nsrc = (int)gsrc.size();
+        l_ent.resize(l_ent.size() + (size_t)g.maxlen * kListTargets, 0);
+        for (int m = 0; m < g.ntgt; ++m) {
+          const auto& pl = pool[members[m]].second;
+          l_tgt.push_back(pool[members[m]].first);
+          l_len.push_back((int)pl.size());
+          for (size_t j = 0; j < pl.size(); ++j)
+            l_ent[g.ent_off + j * kListTargets + m] = (slot.at(pl[j] >> 9) << 9) | (pl[j] & 511);
+        }
+        l_src.insert(l_src.end(), gsrc.begin(), gsrc.end());
+        max_group_src = std::max(max_group_src, g.nsrc);
+        groups.push_back(g);
       }
     }
     if (count) {
@@ -723,6 +796,13 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     ph.src_ids = ar.add(src_ids);
     ph.tgt_ids = ar.add(tgt_ids);
     ph.pmap = ar.add(pmap);
+    ph.n_groups = (int)groups.size();
+    ph.max_group_src = max_group_src;
+    ph.groups = ar.add(groups);
+    ph.l_tgt = ar.add(l_tgt);
+    ph.l_len = ar.add(l_len);
+    ph.l_ent = ar.add(l_ent);
+    ph.l_src = ar.add(l_src);
     ph.n_inv = (int)inv_gid.size();
     ph.inv_sid = ar.add(inv_sid);
     ph.inv_gid = ar.add(inv_gid);
@@ -1066,6 +1146,10 @@ cudaError_t enqueue_fmm(flgf_blockset* bs, const PhaseOff& ph, R* unodes) {
     KRUN(ph.n_work, launch_hadamard<R>(N, ar.at<HadTile>(ph.tiles), ar.at<HadWork>(ph.work), ph.n_work,
                                        ph.max_cells_cpc, ar.at<int>(ph.src_ids), ar.at<int>(ph.tgt_ids),
                                        ar.at<int2>(ph.pmap), bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
+    KRUN(ph.n_groups, launch_hadamard_list<R>(N, ar.at<ListGroup>(ph.groups), ph.n_groups, ph.max_group_src,
+                                              ar.at<int>(ph.l_tgt), ar.at<int>(ph.l_len), ar.at<int>(ph.l_ent),
+                                              ar.at<int>(ph.l_src), bs->spec, bs->acc, ph.nblocks, c->d_kspec,
+                                              c->kstride, s));
   }
   {
     StageScope sc(bs, 4);
@@ -1216,6 +1300,27 @@ void collect_times(flgf_blockset* bs) {
 }
 
 }  // namespace
+
+extern "C" int flgf_ctx_set_option(flgf_ctx* ctx, int key, int value) {
+  if (!ctx) return FLGF_EINVAL;
+  switch (key) {
+    case FLGF_CTX_LIST_PCT:
+      if (value < 0 || value > 100) return fail(ctx, FLGF_EINVAL, "list percentage must be 0..100");
+      ctx->list_pct = value;
+      return FLGF_OK;
+    case FLGF_CTX_TILE: {
+      const int t[3] = {value & 255, (value >> 8) & 255, (value >> 16) & 255};
+      for (int a = 0; a < 3; ++a)
+        if (t[a] < 1 || t[a] > 8) return fail(ctx, FLGF_EINVAL, "tile extents must be 1..8 parents");
+      if (value >> 24 || t[0] * t[1] * t[2] > 128 || (t[0] + 2) * (t[1] + 2) * (t[2] + 2) > 397)
+        return fail(ctx, FLGF_EINVAL, "tile too large for the spectrum MAC");
+      for (int a = 0; a < 3; ++a) ctx->tile[a] = t[a];
+      return FLGF_OK;
+    }
+    default:
+      return fail(ctx, FLGF_EINVAL, "unknown context option");
+  }
+}
 
 extern "C" int flgf_set_option(flgf_blockset* bs, int key, int value) {
   if (!bs) return FLGF_EINVAL;

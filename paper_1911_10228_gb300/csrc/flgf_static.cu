@@ -137,7 +137,7 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
   std::vector<double> scales(nblk, h * h);
   tl.pmap_off = 0;
   std::vector<int2> pmap;
-  build_parent_map(tl, src.data(), pmap);
+  build_parent_map(tl, src.data(), tgt.data(), pmap);
   std::vector<HadTile> tiles(1, tl);
   std::vector<unsigned char> lists;
   const size_t o_tiles = put(lists, tiles), o_work = put(lists, work), o_src = put(lists, src), o_tgt = put(lists, tgt);

@@ -174,18 +174,119 @@ cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, in
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Sparse tiles: each thread walks the explicit pair list of one target for TT
+// frequencies.  Shared memory holds this chunk of the 343 kernel spectra and
+// of the group's sources, so the loop reads only shared memory.
+// ---------------------------------------------------------------------------
+template <typename R, int TT>
+__global__ void __launch_bounds__(kListTargets * 2) hadamard_list_kernel(const ListGroup* __restrict__ groups,
+                                                                       const int* __restrict__ tgt,
+                                                                       const int* __restrict__ len,
+                                                                       const int* __restrict__ ent,
+                                                                       const int* __restrict__ src,
+                                                                       const cplx<R>* __restrict__ spec,
+                                                                       cplx<R>* __restrict__ acc, int spec_blocks,
+                                                                       const cplx<R>* __restrict__ kspec,
+                                                                       size_t kstride) {
+  constexpr int T = ChunkT<R>::value;
+  constexpr int NG = T / TT;
+  static_assert(NG == 2, "two frequency groups per chunk");
+  extern __shared__ __align__(16) int4 sm4[];
+  const ListGroup gr = groups[blockIdx.x];
+  const int chunk = blockIdx.y;
+  const int tid = threadIdx.x;
+  constexpr int KV = kNOff * T * (int)sizeof(cplx<R>) / 16;  // 16-byte vectors of one kernel chunk
+  // frequency-group-major ([NG][343], [NG][nsrc]): the lanes of a warp share
+  // g, so their 16-byte reads spread over all eight bank groups
+  int4* Ks = sm4;
+  int4* Fs = sm4 + KV;
+  const int4* kc = reinterpret_cast<const int4*>(kspec + (size_t)gr.level * kstride + (size_t)chunk * kNOff * T);
+  for (int i = tid; i < KV; i += blockDim.x) Ks[(i % NG) * kNOff + i / NG] = __ldg(kc + i);
+  const int4* fc = reinterpret_cast<const int4*>(spec + (size_t)chunk * spec_blocks * T);
+  for (int i = tid; i < gr.nsrc * NG; i += blockDim.x)
+    Fs[(i % NG) * gr.nsrc + i / NG] = __ldcg(fc + (size_t)src[gr.src_off + i / NG] * NG + i % NG);
+  __syncthreads();
+  const int ti = tid % kListTargets, g = tid / kListTargets;
+  if (ti >= gr.ntgt) return;
+  const int n = len[gr.len_off + ti];
+  const int* e = ent + gr.ent_off + ti;
+  R ar[TT], ai[TT];
+#pragma unroll
+  for (int t = 0; t < TT; ++t) { ar[t] = R(0); ai[t] = R(0); }
+#pragma unroll 4
+  for (int j = 0; j < n; ++j) {
+    const int w = __ldg(e + j * kListTargets);
+    const int4 fv = Fs[g * gr.nsrc + (w >> 9)];
+    const int4 kv = Ks[g * kNOff + (w & 511)];
+    const cplx<R>* f = reinterpret_cast<const cplx<R>*>(&fv);
+    const cplx<R>* k = reinterpret_cast<const cplx<R>*>(&kv);
+#pragma unroll
+    for (int t = 0; t < TT; ++t) {
+      ar[t] = fma(k[t].re, f[t].re, ar[t]);
+      ar[t] = fma(-k[t].im, f[t].im, ar[t]);
+      ai[t] = fma(k[t].re, f[t].im, ai[t]);
+      ai[t] = fma(k[t].im, f[t].re, ai[t]);
+    }
+  }
+  cplx<R>* o = acc + ((size_t)chunk * spec_blocks + tgt[gr.tgt_off + ti]) * T + g * TT;
+#pragma unroll
+  for (int t = 0; t < TT; ++t) o[t] = cplx<R>{ar[t], ai[t]};
+}
+
+template <typename R>
+cudaError_t launch_hadamard_list(int N, const ListGroup* groups, int ngroups, int max_src, const int* tgt,
+                                 const int* len, const int* ent, const int* src, const void* spec, void* acc,
+                                 int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s) {
+  if (ngroups <= 0) return cudaSuccess;
+  constexpr int T = ChunkT<R>::value;
+  constexpr int TT = (sizeof(R) == 4) ? 2 : 1;
+  const size_t sm = sizeof(cplx<R>) * T * ((size_t)kNOff + max_src);
+  if (sm > 200 * 1024) return cudaErrorInvalidConfiguration;
+  static bool attr_set[2] = {false, false};
+  bool& done = attr_set[sizeof(R) == 4 ? 0 : 1];
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute(hadamard_list_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  dim3 grid(ngroups, nchunks<R>(N));
+  hadamard_list_kernel<R, TT><<<grid, kListTargets * 2, sm, s>>>(
+      groups, tgt, len, ent, src, reinterpret_cast<const cplx<R>*>(spec), reinterpret_cast<cplx<R>*>(acc),
+      spec_blocks, reinterpret_cast<const cplx<R>*>(kspec), kspec_level_stride);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_hadamard_list<float>(int, const ListGroup*, int, int, const int*, const int*, const int*,
+                                                 const int*, const void*, void*, int, const void*, size_t,
+                                                 cudaStream_t);
+template cudaError_t launch_hadamard_list<double>(int, const ListGroup*, int, int, const int*, const int*,
+                                                  const int*, const int*, const void*, void*, int, const void*,
+                                                  size_t, cudaStream_t);
+
 template cudaError_t launch_hadamard<float>(int, const HadTile*, const HadWork*, int, int, const int*, const int*,
                                             const int2*, const void*, void*, int, const void*, size_t, cudaStream_t);
 template cudaError_t launch_hadamard<double>(int, const HadTile*, const HadWork*, int, int, const int*, const int*,
                                              const int2*, const void*, void*, int, const void*, size_t, cudaStream_t);
 
-void build_parent_map(const HadTile& tl, const int* src_slots, std::vector<int2>& out) {
+void build_parent_map(const HadTile& tl, const int* src_slots, const int* tgt_slots, std::vector<int2>& out) {
   const int np = tl.P[0] * tl.P[1] * tl.P[2];
   const int NQ = tl.Rg[0] * tl.Rg[1] * tl.Rg[2];
   std::vector<int2> m(np);
   for (int pl = 0; pl < np; ++pl) {
     const int pq[3] = {pl / (tl.P[1] * tl.P[2]), (pl / tl.P[2]) % tl.P[1], pl % tl.P[2]};
     unsigned mask = 0;
+    bool has_tgt = false;  // a parent without targets does no work
+    for (int a = 0; a < 8; ++a) {
+      const int cell = ((2 * pq[0] + (a >> 2)) * 2 * tl.P[1] + (2 * pq[1] + ((a >> 1) & 1))) * 2 * tl.P[2] +
+                       (2 * pq[2] + (a & 1));
+      has_tgt |= tgt_slots[cell] >= 0;
+    }
+    if (!has_tgt) {
+      m[pl] = make_int2(pl, 0);
+      continue;
+    }
     for (int e = 0; e < 27; ++e) {
       if (tl.excl_near && e == 13) continue;
       int n[3];

@@ -77,7 +77,28 @@ cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, in
                             int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s);
 // Parent map of one tile: per parent slot (spatial order) the mask of
 // neighbour parents e that lie in the region and hold at least one source.
-void build_parent_map(const HadTile& tl, const int* src_slots, std::vector<int2>& out);
+void build_parent_map(const HadTile& tl, const int* src_slots, const int* tgt_slots, std::vector<int2>& out);
+// Sparse tiles: explicit (target, source) pair lists.  A group holds up to
+// kListTargets existing targets of one tile (sorted by list length), the
+// union of their existing sources, and per target its pair entries
+// (local source slot << 9 | kernel offset index), stored entry-major
+// [entry][kListTargets] so a warp reads consecutive words.
+constexpr int kListTargets = 128;
+constexpr int kListMaxSrc = 1400;  // sources per group: (343 + 1400) x 32 B of shared memory
+struct ListGroup {
+  int level;     // octree level (kernel spectra)
+  int ntgt;      // targets in the group (<= kListTargets)
+  int maxlen;    // longest pair list
+  int tgt_off;   // into the target list: spectrum column per target
+  int len_off;   // into the length list: pairs per target
+  int ent_off;   // into the entry list: maxlen * kListTargets words
+  int src_off;   // into the source list: spectrum column per local source slot
+  int nsrc;
+};
+template <typename R>
+cudaError_t launch_hadamard_list(int N, const ListGroup* groups, int ngroups, int max_src, const int* tgt,
+                                 const int* len, const int* ent, const int* src, const void* spec, void* acc,
+                                 int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s);
 // Threads per CTA of the spectrum MAC, and the most frequency chunks one CTA takes.
 constexpr int kHadThreads = 256;
 constexpr int kHadMaxCpc = 4;

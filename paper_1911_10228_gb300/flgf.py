@@ -60,6 +60,7 @@ PROTOTYPES = {
     "flgf_laplacian": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int]),
     "flgf_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "flgf_ctx_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "flgf_stage_times": (ctypes.c_int, [ctypes.c_void_p, _c_dbl_p, ctypes.c_int, _c_int_p, ctypes.c_int]),
     "flgf_work_counts": (ctypes.c_int, [ctypes.c_void_p, _c_i64_p, _c_i64_p, _c_i64_p, _c_i64_p]),
     "flgf_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
@@ -123,11 +124,25 @@ class Context:
         if rc != 0:
             raise FLGFError(f"flgf_create failed with code {rc}")
         self.handle = h
+        self.plan = (30, (4, 4, 8))  # (pair-list percentage, dense tile): the library's defaults
 
     def check(self, rc: int, what: str):
         if rc != 0:
             msg = self.lib.flgf_last_error(self.handle).decode()
             raise FLGFError(f"{what} failed ({rc}): {msg}")
+
+    def set_plan(self, list_pct: int | None = None, tile=None):
+        """Plan options for block sets created afterwards: the useful-pair
+        percentage below which a tile runs on the pair-list MAC, and the dense
+        MAC tile (t0, t1, t2) in parents."""
+        if list_pct is not None:
+            self.check(self.lib.flgf_ctx_set_option(self.handle, 1, int(list_pct)), "flgf_ctx_set_option")
+            self.plan = (int(list_pct), self.plan[1])
+        if tile is not None:
+            t = [int(v) for v in tile]
+            self.check(self.lib.flgf_ctx_set_option(self.handle, 2, t[0] | t[1] << 8 | t[2] << 16),
+                       "flgf_ctx_set_option")
+            self.plan = (self.plan[0], tuple(t))
 
     def lgf(self, pts) -> np.ndarray:
         pts = np.ascontiguousarray(np.asarray(pts, dtype=np.int32).reshape(-1, 3))

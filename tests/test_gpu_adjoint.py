@@ -55,14 +55,17 @@ def test_adjoint_matches_oracle(G, precision, correction, tol):
         assert err < tol, (l, err)
 
 
-def test_dot_product_identity_fp64():
-    """<A f, g> = <f, A^T g> on the GPU alone (sources on leaf blocks only)."""
+@pytest.mark.parametrize("list_pct", [30, 0, 100], ids=["default", "dense", "list"])
+def test_dot_product_identity_fp64(list_pct):
+    """<A f, g> = <f, A^T g> on the GPU alone (sources on leaf blocks only),
+    with the spectrum MAC on the dense kernel, the pair-list kernel or both."""
     p = _mesh()
     leaf = p.leaf_masks()
     rng = np.random.default_rng(22)
     f = [np.where(m[:, None, None, None], rng.standard_normal((len(c), 8, 8, 8)), 0.0) for c, m in zip(p.coords, leaf)]
     g = [rng.standard_normal((len(c), 8, 8, 8)) for c in p.coords]
     c = F.Context(N=8, n_interp=6, precision="fp64")
+    c.set_plan(list_pct=list_pct)
     bs = F.BlockSet(c, [p.coords], [p.h0])
     for l in range(p.n_levels):
         bs.load_source(0, l, torch.as_tensor(f[l]))

@@ -13,11 +13,20 @@ pytestmark = pytest.mark.gpu
 _REF = {}
 
 
+# plan: (pair-list percentage, dense tile); 0 sends every tile to the dense
+# parent-group kernel, 100 every tile that is not completely full to the
+# pair-list kernel
+PLANS = [None, (0, (4, 4, 8)), (100, (2, 4, 8)), (50, (4, 4, 4))]
+
+
+@pytest.mark.parametrize("plan", PLANS, ids=["default", "dense", "list", "mixed"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
-def test_random_sparse_batch_matches_oracle(G, precision, tol):
+def test_random_sparse_batch_matches_oracle(G, precision, tol, plan):
     probs = [random_sparse_problem(s, N=8, nblk_range=(8, 120)) for s in (1, 4, 7, 9)]
     assert max(p.n_levels for p in probs) >= 2
     c = F.Context(N=8, n_interp=6, precision=precision)
+    if plan is not None:
+        c.set_plan(list_pct=plan[0], tile=plan[1])
     bs = F.BlockSet(c, [p.coords for p in probs], [p.h0 for p in probs])
     for i, p in enumerate(probs):
         for l, f in enumerate(p.f):
@@ -33,4 +42,14 @@ def test_random_sparse_batch_matches_oracle(G, precision, tol):
             u = bs.potential(i, l).double().cpu().numpy()
             assert np.max(np.abs(u[leaf[l]] - ref[l][leaf[l]])) < tol * scale, (i, l)
     bs.close()
+    c.close()
+
+
+def test_plan_options_are_validated():
+    c = F.Context(N=8, n_interp=4, precision="fp32")
+    for bad in (dict(list_pct=-1), dict(list_pct=101), dict(tile=(0, 4, 4)), dict(tile=(8, 8, 8)),
+                dict(tile=(2, 8, 8))):
+        with pytest.raises(F.FLGFError):
+            c.set_plan(**bad)
+    c.set_plan(list_pct=0, tile=(8, 4, 4))
     c.close()
