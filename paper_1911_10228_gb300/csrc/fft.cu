@@ -161,12 +161,34 @@ __global__ void __launch_bounds__(N * N) fft_fwd_kernel(const R* __restrict__ no
   const R* in = nodes + (size_t)gid * N * N * N;
   const int tid = threadIdx.x;
 
+  // stage the block with coalesced 16-byte loads: plane z goes to the rows
+  // y >= N of plane z of the buffer, which axis 2 leaves untouched.  Staged
+  // rows are SU (odd) 16-byte vectors apart, so the 8 lanes of a quarter warp
+  // reading 8 consecutive rows hit 8 different bank groups.
+  constexpr int V = 16 / (int)sizeof(R);  // values per 16-byte vector
+  constexpr int RV = N / V;               // vectors per row
+  constexpr int SU = RV + 1;              // staged row stride in vectors
+  static_assert(N * SU * 16 <= N * NX * (int)sizeof(cplx<R>), "staged plane fits the unused rows");
+  {
+    const int4* src = reinterpret_cast<const int4*>(in);
+    for (int i = tid; i < N * N * RV; i += blockDim.x) {
+      const int z = i / (N * RV), y = (i / RV) % N, u = i % RV;
+      reinterpret_cast<int4*>(buf + (z * P + N) * NX)[y * SU + u] = __ldg(src + i);
+    }
+  }
+  __syncthreads();
   // axis 2 (real input, N of 2N nonzero)
   for (int line = tid; line < N * N; line += blockDim.x) {
     const int z = line / N, y = line % N;
     R xr[N], xi[N];
+    const int4* stage = reinterpret_cast<const int4*>(buf + (z * P + N) * NX) + y * SU;
 #pragma unroll
-    for (int x = 0; x < N; ++x) { xr[x] = in[(z * N + y) * N + x]; xi[x] = R(0); }
+    for (int u = 0; u < RV; ++u) {
+      const int4 v = stage[u];
+      const R* r = reinterpret_cast<const R*>(&v);
+#pragma unroll
+      for (int j = 0; j < V; ++j) { xr[u * V + j] = r[j]; xi[u * V + j] = R(0); }
+    }
     cplx<R>* row = buf + (z * P + y) * NX;
     fft_fwd_pruned<P>(xr, xi, [&](int k, R re, R im) {
       if (k <= N) row[k] = cplx<R>{re, im};
@@ -257,8 +279,16 @@ __global__ void __launch_bounds__(N * N) fft_inv_kernel(const cplx<R>* __restric
     for (int k = N + 1; k < P; ++k) { Xr[k] = Xr[P - k]; Xi[k] = -Xi[P - k]; }
     R xr[N], xi[N];
     fft_inv_pruned<P>(Xr, Xi, xr, xi);
+    constexpr int V = 16 / (int)sizeof(R);
+    int4* orow = reinterpret_cast<int4*>(o + (z * N + y) * N);
 #pragma unroll
-    for (int x = 0; x < N; ++x) o[(z * N + y) * N + x] = scale * xr[x];
+    for (int u = 0; u < N / V; ++u) {
+      int4 v;
+      R* r = reinterpret_cast<R*>(&v);
+#pragma unroll
+      for (int j = 0; j < V; ++j) r[j] = scale * xr[u * V + j];
+      orow[u] = v;
+    }
   }
 }
 

@@ -66,12 +66,13 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
     Ks[i] = __ldg(reinterpret_cast<const int4*>(kspec + (size_t)tl.level * kstride + (size_t)(wk.chunk0 + cs) * kNOff * T) + v);
   }
   for (int cs = 0; cs < wk.nch; ++cs) {
-    const int4* fsrc = reinterpret_cast<const int4*>(spec + (size_t)(wk.chunk0 + cs) * spec_blocks * T);
     int4* fdst = Fs + (size_t)cs * NG * S;
     for (int i = tid; i < S * NG; i += kHadThreads) {
       const int slot = i / NG, g = i % NG;
       const int sid = src_ids[tl.src_off + slot];
-      fdst[g * S + slot] = sid >= 0 ? __ldcg(fsrc + (size_t)sid * NG + g) : make_int4(0, 0, 0, 0);
+      fdst[g * S + slot] =
+          sid >= 0 ? __ldcg(reinterpret_cast<const int4*>(spec + chunk_offset<R>(wk.chunk0 + cs, sid, spec_blocks)) + g)
+                   : make_int4(0, 0, 0, 0);
     }
   }
   __syncthreads();
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
     const int cell = ((2 * pq[0] + a0) * TP1 + (2 * pq[1] + a1)) * TP2 + (2 * pq[2] + a2);
     const int sid = tgt_ids[tl.tgt_off + cell];
     if (sid < 0) continue;
-    cplx<R>* o = acc + ((size_t)chunk * spec_blocks + sid) * T + f0;
+    cplx<R>* o = acc + chunk_offset<R>(chunk, sid, spec_blocks) + f0;
 #pragma unroll
     for (int t = 0; t < TT; ++t) o[t] = cplx<R>{ar[a][t], ai[a][t]};
   }
@@ -203,9 +204,9 @@ __global__ void __launch_bounds__(kListTargets * 2) hadamard_list_kernel(const L
   int4* Fs = sm4 + KV;
   const int4* kc = reinterpret_cast<const int4*>(kspec + (size_t)gr.level * kstride + (size_t)chunk * kNOff * T);
   for (int i = tid; i < KV; i += blockDim.x) Ks[(i % NG) * kNOff + i / NG] = __ldg(kc + i);
-  const int4* fc = reinterpret_cast<const int4*>(spec + (size_t)chunk * spec_blocks * T);
   for (int i = tid; i < gr.nsrc * NG; i += blockDim.x)
-    Fs[(i % NG) * gr.nsrc + i / NG] = __ldcg(fc + (size_t)src[gr.src_off + i / NG] * NG + i % NG);
+    Fs[(i % NG) * gr.nsrc + i / NG] =
+        __ldcg(reinterpret_cast<const int4*>(spec + chunk_offset<R>(chunk, src[gr.src_off + i / NG], spec_blocks)) + i % NG);
   __syncthreads();
   const int ti = tid % kListTargets, g = tid / kListTargets;
   if (ti >= gr.ntgt) return;
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(kListTargets * 2) hadamard_list_kernel(const L
       ai[t] = fma(k[t].im, f[t].re, ai[t]);
     }
   }
-  cplx<R>* o = acc + ((size_t)chunk * spec_blocks + tgt[gr.tgt_off + ti]) * T + g * TT;
+  cplx<R>* o = acc + chunk_offset<R>(chunk, tgt[gr.tgt_off + ti], spec_blocks) + g * TT;
 #pragma unroll
   for (int t = 0; t < TT; ++t) o[t] = cplx<R>{ar[t], ai[t]};
 }
