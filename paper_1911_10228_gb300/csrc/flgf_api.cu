@@ -133,7 +133,8 @@ struct PhaseOff {  // arena offsets and counts of one phase's launch lists
   int n_prep = 0; size_t prep_src = 0, prep_dst = 0, prep_zero = 0;
   std::vector<int> n_ant; std::vector<size_t> ant_par, ant_ch;
   int n_fwd = 0; size_t fwd_gid = 0, fwd_sid = 0;
-  int n_tiles = 0, n_work = 0, max_cells_cpc = 0; size_t tiles = 0, work = 0, src_ids = 0, tgt_ids = 0, pmap = 0;
+  int n_groups_dense = 0, n_work = 0, max_units = 0;
+  size_t hgroups = 0, work = 0, src_ids = 0, tgt_ids = 0, par_tab = 0;
   int n_groups = 0, max_group_src = 0; size_t groups = 0, l_tgt = 0, l_len = 0, l_ent = 0, l_src = 0;
   int n_inv = 0; size_t inv_sid = 0, inv_gid = 0, inv_scale = 0;
   std::vector<int> n_itp; std::vector<size_t> itp_ch, itp_par, itp_cpos;
@@ -553,10 +554,8 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     std::vector<std::vector<int>> itp_ch(maxtop + 1), itp_par(maxtop + 1), itp_cpos(maxtop + 1);
     std::vector<int> fwd_gid, fwd_sid, inv_sid, inv_gid;
     std::vector<double> inv_scale;
-    std::vector<HadTile> tiles;
-    std::vector<HadWork> work;
-    std::vector<int> src_ids, tgt_ids;
-    std::vector<int2> pmap;
+    // parents with targets of dense tiles per octree level, in tile order
+    std::vector<std::vector<ParentRec>> dpool;
     std::vector<ListGroup> groups;
     std::vector<int> l_tgt, l_len, l_ent, l_src;
     int max_group_src = 0;
@@ -617,12 +616,9 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
         for (int t0 = lo[0]; t0 <= hi[0]; t0 += TP[0])
           for (int t1 = lo[1]; t1 <= hi[1]; t1 += TP[1])
             for (int t2 = lo[2]; t2 <= hi[2]; t2 += TP[2]) {
-              HadTile tl;
-              tl.level = (int)k;
-              tl.excl_near = excl ? 1 : 0;
+              struct { int P[3], r0[3], Rg[3]; } tl;  // tile and its region (tile + 1 parent, clipped)
               const int t[3] = {t0, t1, t2};
               for (int a = 0; a < 3; ++a) {
-                tl.p0[a] = t[a];
                 tl.P[a] = std::min(TP[a], hi[a] - t[a] + 1);
                 tl.r0[a] = std::max(t[a] - 1, lo[a]);
                 tl.Rg[a] = std::min(t[a] + tl.P[a], hi[a]) - tl.r0[a] + 1;
@@ -681,10 +677,38 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
                     useful += (int64_t)plist[ti].size();
                   }
               if (count) bs->pairs += useful;
-              std::vector<int2> tpm;
-              build_parent_map(tl, sg.data(), tg.data(), tpm);
+              // parent records of the tile's parents that have targets
+              std::vector<ParentRec> recs;
               int64_t dense = 0;  // complex MACs per frequency of the parent-group kernel
-              for (const int2& m : tpm) dense += 64 * (int64_t)__builtin_popcount((unsigned)m.y);
+              for (int p0 = 0; p0 < tl.P[0]; ++p0)
+                for (int p1 = 0; p1 < tl.P[1]; ++p1)
+                  for (int p2 = 0; p2 < tl.P[2]; ++p2) {
+                    ParentRec r;
+                    bool has = false;
+                    for (int a = 0; a < 8; ++a) {
+                      r.tgt[a] = tg[((2 * p0 + (a >> 2)) * 2 * tl.P[1] + 2 * p1 + ((a >> 1) & 1)) * 2 * tl.P[2] + 2 * p2 +
+                                    (a & 1)];
+                      has |= r.tgt[a] >= 0;
+                    }
+                    if (!has) continue;
+                    const int pc[3] = {t0 + p0, t1 + p1, t2 + p2};
+                    for (int e = 0; e < 27; ++e) {
+                      const int ee[3] = {e / 9 - 1, (e / 3) % 3 - 1, e % 3 - 1};
+                      int q[3];
+                      bool inr = !(excl && e == 13);
+                      for (int a = 0; a < 3; ++a) {
+                        q[a] = pc[a] + ee[a] - tl.r0[a];
+                        inr &= q[a] >= 0 && q[a] < tl.Rg[a];
+                      }
+                      bool any_src = false;
+                      for (int b = 0; b < 8; ++b) {
+                        r.cell[e][b] = inr ? sg[b * NQ + (q[0] * tl.Rg[1] + q[1]) * tl.Rg[2] + q[2]] : -1;
+                        any_src |= r.cell[e][b] >= 0;
+                      }
+                      dense += any_src ? 64 : 0;
+                    }
+                    recs.push_back(r);
+                  }
               if (useful * 100 < (int64_t)ctx->list_pct * dense) {
                 // sparse tile: its targets join the pair-list pool of octree level k
                 if ((int)lpool.size() <= (int)k) lpool.resize(k + 1);
@@ -692,27 +716,14 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
                   if (tg[ti] >= 0) lpool[k].push_back({tg[ti], std::move(plist[ti])});
                 continue;
               }
-              // threads: (parent slot, frequency group, chunk); small tiles take
-              // several chunks per CTA, bounded by shared memory (~100 KB)
-              const int np = tl.P[0] * tl.P[1] * tl.P[2];
-              tl.pslots = 1;
-              while (tl.pslots < np) tl.pslots <<= 1;
-              int cpc = std::min(kHadMaxCpc, kHadThreads / (tl.pslots * 2));
-              while (cpc > 1 && (8 * NQ + kNOff) * cpc > 3520) cpc >>= 1;  // <= 110 KB shared
-              tl.cpc = cpc;
-              ph.max_cells_cpc = std::max(ph.max_cells_cpc, (8 * NQ + kNOff) * cpc);
-              for (int c0 = 0; c0 < nchunk; c0 += cpc)
-                work.push_back(HadWork{(int)tiles.size(), c0, std::min(cpc, nchunk - c0)});
-              tl.tgt_off = (int)tgt_ids.size();
-              tgt_ids.insert(tgt_ids.end(), tg.begin(), tg.end());
-              tl.src_off = (int)src_ids.size();
-              src_ids.insert(src_ids.end(), sg.begin(), sg.end());
-              tl.pmap_off = (int)pmap.size();
-              pmap.insert(pmap.end(), tpm.begin(), tpm.end());
-              tiles.push_back(tl);
+              if ((int)dpool.size() <= (int)k) dpool.resize(k + 1);
+              dpool[k].insert(dpool[k].end(), recs.begin(), recs.end());
             }
       }
     }
+    // dense MAC: parent groups of every octree level
+    HadLists hl;
+    for (int k = 0; k < (int)dpool.size(); ++k) pack_parent_groups(k, dpool[k], nchunk, hl);
     // pair-list groups: consecutive pool targets (spatially close, so their
     // source sets overlap) up to kListTargets targets or kListMaxSrc sources
     for (int k = 0; k < (int)lpool.size(); ++k) {
@@ -786,16 +797,18 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     ph.n_fwd = (int)fwd_gid.size();
     ph.fwd_gid = ar.add(fwd_gid);
     ph.fwd_sid = ar.add(fwd_sid);
-    ph.n_tiles = (int)tiles.size();
-    ph.tiles = ar.add(tiles);
-    // chunk-major order: the tiles sharing a frequency chunk run back to back,
+    ph.n_groups_dense = (int)hl.groups.size();
+    ph.hgroups = ar.add(hl.groups);
+    ph.max_units = hl.max_units;
+    std::vector<HadWork>& work = hl.work;
+    // chunk-major order: the groups sharing a frequency chunk run back to back,
     // so the chunk's kernel spectra and the shared halo spectra stay in L2
     std::stable_sort(work.begin(), work.end(), [](const HadWork& x, const HadWork& y) { return x.chunk0 < y.chunk0; });
     ph.n_work = (int)work.size();
     ph.work = ar.add(work);
-    ph.src_ids = ar.add(src_ids);
-    ph.tgt_ids = ar.add(tgt_ids);
-    ph.pmap = ar.add(pmap);
+    ph.src_ids = ar.add(hl.src_ids);
+    ph.tgt_ids = ar.add(hl.tgt_ids);
+    ph.par_tab = ar.add(hl.par_tab);
     ph.n_groups = (int)groups.size();
     ph.max_group_src = max_group_src;
     ph.groups = ar.add(groups);
@@ -1143,9 +1156,10 @@ cudaError_t enqueue_fmm(flgf_blockset* bs, const PhaseOff& ph, R* unodes) {
   }
   {
     StageScope sc(bs, 3);
-    KRUN(ph.n_work, launch_hadamard<R>(N, ar.at<HadTile>(ph.tiles), ar.at<HadWork>(ph.work), ph.n_work,
-                                       ph.max_cells_cpc, ar.at<int>(ph.src_ids), ar.at<int>(ph.tgt_ids),
-                                       ar.at<int2>(ph.pmap), bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
+    KRUN(ph.n_work, launch_hadamard<R>(N, ar.at<HadGroup>(ph.hgroups), ar.at<HadWork>(ph.work), ph.n_work,
+                                       ph.max_units, ar.at<int>(ph.src_ids), ar.at<int>(ph.tgt_ids),
+                                       ar.at<int16_t>(ph.par_tab), bs->spec, bs->acc, ph.nblocks, c->d_kspec,
+                                       c->kstride, s));
     KRUN(ph.n_groups, launch_hadamard_list<R>(N, ar.at<ListGroup>(ph.groups), ph.n_groups, ph.max_group_src,
                                               ar.at<int>(ph.l_tgt), ar.at<int>(ph.l_len), ar.at<int>(ph.l_ent),
                                               ar.at<int>(ph.l_src), bs->spec, bs->acc, ph.nblocks, c->d_kspec,

@@ -102,46 +102,35 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
       if (c[b][0] == x && c[b][1] == y && c[b][2] == z) return b;
     return -1;
   };
-  // launch lists: one tile covering the parent box; its region is the same box
-  HadTile tl;
-  tl.level = 0;
-  tl.excl_near = 0;
-  for (int a = 0; a < 3; ++a) {
-    tl.p0[a] = plo[a];
-    tl.P[a] = phi[a] - plo[a] + 1;
-    tl.r0[a] = plo[a];
-    tl.Rg[a] = tl.P[a];
-  }
-  const int NQ = tl.Rg[0] * tl.Rg[1] * tl.Rg[2];
-  std::vector<int> src(8 * NQ, -1), tgt;
-  for (int x = 0; x < 2 * tl.P[0]; ++x)
-    for (int y = 0; y < 2 * tl.P[1]; ++y)
-      for (int z = 0; z < 2 * tl.P[2]; ++z) {
-        const int b = find(2 * plo[0] + x, 2 * plo[1] + y, 2 * plo[2] + z);
-        tgt.push_back(b);
-        const int slot = (((x & 1) << 2) | ((y & 1) << 1) | (z & 1)) * NQ + ((x >> 1) * tl.Rg[1] + (y >> 1)) * tl.Rg[2] + (z >> 1);
-        src[slot] = b;
+  // launch lists: one parent group over the parent box (one octree level,
+  // near field included: every pair is a neighbour-parent pair)
+  std::vector<ParentRec> recs;
+  for (int p0 = plo[0]; p0 <= phi[0]; ++p0)
+    for (int p1 = plo[1]; p1 <= phi[1]; ++p1)
+      for (int p2 = plo[2]; p2 <= phi[2]; ++p2) {
+        ParentRec r;
+        bool has = false;
+        for (int a = 0; a < 8; ++a) {
+          r.tgt[a] = find(2 * p0 + (a >> 2), 2 * p1 + ((a >> 1) & 1), 2 * p2 + (a & 1));
+          has |= r.tgt[a] >= 0;
+        }
+        if (!has) continue;
+        for (int e = 0; e < 27; ++e)
+          for (int b = 0; b < 8; ++b)
+            r.cell[e][b] = find(2 * (p0 + e / 9 - 1) + (b >> 2), 2 * (p1 + (e / 3) % 3 - 1) + ((b >> 1) & 1),
+                                2 * (p2 + e % 3 - 1) + (b & 1));
+        recs.push_back(r);
       }
-  tl.src_off = 0;
-  tl.tgt_off = 0;
-  tl.pslots = 1;
-  while (tl.pslots < tl.P[0] * tl.P[1] * tl.P[2]) tl.pslots <<= 1;
-  int cpc = std::min(kHadMaxCpc, kHadThreads / (tl.pslots * 2));
-  while (cpc > 1 && (8 * NQ + kNOff) * cpc > 3520) cpc >>= 1;  // <= 110 KB shared
-  tl.cpc = cpc;
   const int nchunk = cv.fp64 ? nchunks<double>(N) : nchunks<float>(N);
-  std::vector<HadWork> work;
-  for (int c0 = 0; c0 < nchunk; c0 += cpc) work.push_back(HadWork{0, c0, std::min(cpc, nchunk - c0)});
+  HadLists hl;
+  pack_parent_groups(0, recs, nchunk, hl);
   std::vector<int> ids(nblk);
   for (int b = 0; b < nblk; ++b) ids[b] = b;
   std::vector<double> scales(nblk, h * h);
-  tl.pmap_off = 0;
-  std::vector<int2> pmap;
-  build_parent_map(tl, src.data(), tgt.data(), pmap);
-  std::vector<HadTile> tiles(1, tl);
   std::vector<unsigned char> lists;
-  const size_t o_tiles = put(lists, tiles), o_work = put(lists, work), o_src = put(lists, src), o_tgt = put(lists, tgt);
-  const size_t o_ids = put(lists, ids), o_scale = put(lists, scales), o_pmap = put(lists, pmap);
+  const size_t o_groups = put(lists, hl.groups), o_work = put(lists, hl.work), o_src = put(lists, hl.src_ids),
+               o_tgt = put(lists, hl.tgt_ids), o_par = put(lists, hl.par_tab);
+  const size_t o_ids = put(lists, ids), o_scale = put(lists, scales);
   if (lists.size() > kListBytes) return bad(FLGF_EINVAL, "convolve_static: launch lists exceed the scratch");
 
   void* base = nullptr;
@@ -160,16 +149,17 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
     else e = launch_fft_forward<float>(N, static_cast<const float*>(f), d_ids, d_ids, nblk, spec, nblk, s);
   }
   if (e == cudaSuccess) {
-    const HadTile* d_tiles = reinterpret_cast<const HadTile*>(dl + o_tiles);
+    const HadGroup* d_groups = reinterpret_cast<const HadGroup*>(dl + o_groups);
     const HadWork* d_work = reinterpret_cast<const HadWork*>(dl + o_work);
     const int* d_src = reinterpret_cast<const int*>(dl + o_src);
     const int* d_tgt = reinterpret_cast<const int*>(dl + o_tgt);
-    const int2* d_pmap = reinterpret_cast<const int2*>(dl + o_pmap);
+    const int16_t* d_par = reinterpret_cast<const int16_t*>(dl + o_par);
+    const int nw = (int)hl.work.size();
     if (cv.fp64)
-      e = launch_hadamard<double>(N, d_tiles, d_work, (int)work.size(), (8 * NQ + kNOff) * cpc, d_src, d_tgt, d_pmap, spec, acc, nblk,
+      e = launch_hadamard<double>(N, d_groups, d_work, nw, hl.max_units, d_src, d_tgt, d_par, spec, acc, nblk,
                                   cv.kspec, cv.kstride, s);
     else
-      e = launch_hadamard<float>(N, d_tiles, d_work, (int)work.size(), (8 * NQ + kNOff) * cpc, d_src, d_tgt, d_pmap, spec, acc, nblk,
+      e = launch_hadamard<float>(N, d_groups, d_work, nw, hl.max_units, d_src, d_tgt, d_par, spec, acc, nblk,
                                  cv.kspec, cv.kstride, s);
   }
   if (e == cudaSuccess) {

@@ -12,25 +12,28 @@
 // used 8 times, and the kernel spectra (indexed by d only) are the same for
 // every thread of a warp (shared-memory broadcast).
 //
-// CTA = (tile of parents) x (cpc chunks of T frequencies), 256 threads: a
-// thread is (parent slot, frequency group, chunk).  Tiles of the coarse
-// octree levels have few parents and take several chunks per CTA so every
-// CTA keeps 8 warps busy.  Shared memory holds, per chunk, the spectra of
-// every source block in the tile's region (tile grown by one parent on each
-// side, clipped to the level's bounding box; absent blocks are zero), stored
-// parity-major -- [chunk][frequency group][child position b][parent cell q]
-// -- so the threads of a warp (consecutive parents) read consecutive 16-byte
-// vectors.  The host orders each tile's source list in that order, so the
-// fill is a straight copy (through L2 only).  The CTA's kernel-spectrum
-// chunks are staged in shared memory too: within a warp every thread needs
-// the same offset d, so each read is one broadcast; per neighbour parent e
-// the 27 distinct offsets are read once each and the 8 source spectra are
-// held in registers.  On
-// levels that exclude the near field, e = 0 (all pairs near) is skipped and
+// Parent groups: the host packs the parents that have targets, in spatial
+// order, into groups of at most 128.  The group's "cells" are the neighbour
+// parents that hold sources, in block order; child b of cell c sits in slot
+// b * ncell + c (zero where the child is absent or no source), so the threads
+// of a warp -- consecutive parents of a full tile -- read consecutive 16-byte
+// vectors.  A table in shared memory gives, per parent and neighbour e, the
+// cell (or none).  Parents without targets and cells without sources take no
+// thread and no shared memory, so sparse meshes keep the threads busy.
+//
+// CTA = (group) x (cpc chunks of T frequencies), 256 threads: a thread is
+// (parent slot, frequency group, chunk).  Groups with few parents take
+// several chunks per CTA so every CTA keeps 8 warps busy.  Shared memory
+// holds, per chunk, the group's source spectra ([chunk][frequency
+// group][slot], filled through L2 only) and the 343 kernel spectra; each
+// thread holds the 8 source spectra of one neighbour cell in registers and
+// reads the 27 distinct offsets d of that cell once each.  On levels that
+// exclude the near field the host gives e = 0 (all pairs near) no cell, and
 // the remaining near offsets |d|_inf <= 1 have zero spectra in the table
 // (set up that way for octree levels >= 1).
 // Complex multiply-adds are written as four fused multiply-adds.
 #include <algorithm>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -39,37 +42,38 @@
 namespace flgf {
 
 template <typename R, int TT>
-__global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile* __restrict__ tiles,
+__global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadGroup* __restrict__ groups,
                                                                   const HadWork* __restrict__ work,
                                                                   const int* __restrict__ src_ids,
                                                                   const int* __restrict__ tgt_ids,
-                                                                  const int2* __restrict__ pmap,
+                                                                  const int16_t* __restrict__ par_tab,
                                                                   const cplx<R>* __restrict__ spec,
                                                                   cplx<R>* __restrict__ acc, int spec_blocks,
                                                                   const cplx<R>* __restrict__ kspec, size_t kstride) {
   constexpr int T = ChunkT<R>::value;
   constexpr int NG = T / TT;  // frequency groups per chunk
-  static_assert(TT * sizeof(cplx<R>) == 16, "one 16-byte vector per (group, cell)");
-  extern __shared__ __align__(16) int4 Fs[];  // [cpc][NG][8 NQ] 16-byte vectors, then [cpc][343][T] kernel spectra
+  static_assert(TT * sizeof(cplx<R>) == 16, "one 16-byte vector per (group, slot)");
+  // [cpc][NG][8][ncell] source vectors, [cpc][343][T] kernel spectra, [27][nact] neighbour cells
+  extern __shared__ __align__(16) int4 Fs[];
   const HadWork wk = work[blockIdx.x];
-  const HadTile tl = tiles[wk.tile];
+  const HadGroup gp = groups[wk.group];
   const int tid = threadIdx.x;
-  const int R1 = tl.Rg[1], R2 = tl.Rg[2];
-  const int NQ = tl.Rg[0] * R1 * R2;
-  const int S = 8 * NQ;  // slots per (chunk, group)
+  const int NC = gp.ncell;
+  const int S = 8 * NC;  // slots per (chunk, group): child b of cell c at b * NC + c
 
-  // this CTA's kernel-spectrum chunks (343 x 32 bytes each) after the source region
-  int4* Ks = Fs + (size_t)tl.cpc * NG * S;
+  int4* Ks = Fs + (size_t)gp.cpc * NG * S;
   constexpr int KV = kNOff * T * (int)sizeof(cplx<R>) / 16;  // 16-byte vectors per chunk
+  int16_t* NB = reinterpret_cast<int16_t*>(Ks + (size_t)gp.cpc * KV);
+  for (int i = tid; i < 27 * gp.nact; i += kHadThreads) NB[i] = par_tab[gp.par_off + i];
   for (int i = tid; i < wk.nch * KV; i += kHadThreads) {
     const int cs = i / KV, v = i % KV;
-    Ks[i] = __ldg(reinterpret_cast<const int4*>(kspec + (size_t)tl.level * kstride + (size_t)(wk.chunk0 + cs) * kNOff * T) + v);
+    Ks[i] = __ldg(reinterpret_cast<const int4*>(kspec + (size_t)gp.level * kstride + (size_t)(wk.chunk0 + cs) * kNOff * T) + v);
   }
   for (int cs = 0; cs < wk.nch; ++cs) {
     int4* fdst = Fs + (size_t)cs * NG * S;
     for (int i = tid; i < S * NG; i += kHadThreads) {
       const int slot = i / NG, g = i % NG;
-      const int sid = src_ids[tl.src_off + slot];
+      const int sid = src_ids[gp.src_off + slot];
       fdst[g * S + slot] =
           sid >= 0 ? __ldcg(reinterpret_cast<const int4*>(spec + chunk_offset<R>(wk.chunk0 + cs, sid, spec_blocks)) + g)
                    : make_int4(0, 0, 0, 0);
@@ -77,18 +81,12 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
   }
   __syncthreads();
 
-  const int slot = tid % tl.pslots;
-  const int g = (tid / tl.pslots) % NG;
-  const int cs = tid / (tl.pslots * NG);
-  const int np = tl.P[0] * tl.P[1] * tl.P[2];
-  if (slot >= np || cs >= wk.nch) return;
-  const int2 pm = pmap[tl.pmap_off + slot];
-  const int pl = pm.x;          // parent index in the tile
-  const unsigned emask = pm.y;  // neighbours e that hold sources
+  const int slot = tid % gp.pslots;
+  const int g = (tid / gp.pslots) % NG;
+  const int cs = tid / (gp.pslots * NG);
+  if (slot >= gp.nact || cs >= wk.nch) return;
   const int chunk = wk.chunk0 + cs;
   const int f0 = g * TT;
-  const int pq[3] = {pl / (tl.P[1] * tl.P[2]), (pl / tl.P[2]) % tl.P[1], pl % tl.P[2]};
-  const int q0 = tl.p0[0] + pq[0] - tl.r0[0], q1 = tl.p0[1] + pq[1] - tl.r0[1], q2 = tl.p0[2] + pq[2] - tl.r0[2];
   const cplx<R>* Fg = reinterpret_cast<const cplx<R>*>(Fs + (size_t)(cs * NG + g) * S);
   const cplx<R>* Kc = reinterpret_cast<const cplx<R>*>(Ks + (size_t)cs * KV) + f0;
 
@@ -98,18 +96,20 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
 #pragma unroll
     for (int t = 0; t < TT; ++t) { ar[a][t] = R(0); ai[a][t] = R(0); }
 
+  int cn = NB[slot];  // the next neighbour's cell is read one iteration ahead
   for (int e = 0; e < 27; ++e) {
-    if (!((emask >> e) & 1u)) continue;  // outside the region, no sources, or e = 0 without near field
+    const int c = cn;
+    if (e + 1 < 27) cn = NB[(e + 1) * gp.nact + slot];
+    if (c < 0) continue;  // no neighbour parent with sources (or e = 0 without near field)
     const int e0 = e / 9 - 1, e1 = (e / 3) % 3 - 1, e2 = e % 3 - 1;
-    const int n0 = q0 + e0, n1 = q1 + e1, n2 = q2 + e2;
-    // the 8 children b of neighbour parent p + e, TT frequencies each
-    const cplx<R>* fb = Fg + (size_t)((n0 * R1 + n1) * R2 + n2) * TT;
+    // the 8 children b of neighbour parent p + e, TT frequencies each (zero where absent)
+    const cplx<R>* fb = Fg + (size_t)c * TT;
     R fr[8][TT], fi[8][TT];
 #pragma unroll
     for (int b = 0; b < 8; ++b)
 #pragma unroll
       for (int t = 0; t < TT; ++t) {
-        const cplx<R> v = fb[(size_t)b * NQ * TT + t];
+        const cplx<R> v = fb[(size_t)b * NC * TT + t];
         fr[b][t] = v.re; fi[b][t] = v.im;
       }
     // d = a - b - 2e takes 27 values delta - 2e (delta = a - b in {-1,0,1}^3):
@@ -136,13 +136,11 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
       }
     }
   }
-  // write the 8 targets
-  const int TP1 = 2 * tl.P[1], TP2 = 2 * tl.P[2];
+  // write the parent's targets
+  const int* tg = tgt_ids + gp.tgt_off + slot * 8;
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
-    const int a0 = a >> 2, a1 = (a >> 1) & 1, a2 = a & 1;
-    const int cell = ((2 * pq[0] + a0) * TP1 + (2 * pq[1] + a1)) * TP2 + (2 * pq[2] + a2);
-    const int sid = tgt_ids[tl.tgt_off + cell];
+    const int sid = __ldg(tg + a);
     if (sid < 0) continue;
     cplx<R>* o = acc + chunk_offset<R>(chunk, sid, spec_blocks) + f0;
 #pragma unroll
@@ -151,24 +149,25 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadTile*
 }
 
 template <typename R>
-cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, int nwork, int max_cells_x_cpc,
-                            const int* src_ids, const int* tgt_ids, const int2* pmap, const void* spec, void* acc,
+cudaError_t launch_hadamard(int N, const HadGroup* groups, const HadWork* work, int nwork, int max_units,
+                            const int* src_ids, const int* tgt_ids, const int16_t* par_tab, const void* spec, void* acc,
                             int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s) {
   if (nwork <= 0) return cudaSuccess;
-  constexpr int T = ChunkT<R>::value;
   constexpr int TT = (sizeof(R) == 4) ? 2 : 1;
-  // per chunk: the source region cells and the 343 kernel spectra (32 bytes each)
-  const size_t sm = sizeof(cplx<R>) * T * (size_t)max_cells_x_cpc;
-  if (sm > 110 * 1024) return cudaErrorInvalidConfiguration;
+  // per chunk the group's source spectra and the 343 kernel spectra, and the
+  // neighbour table: max_units 32-byte units
+  const size_t sm = 32 * (size_t)max_units;
+  if (sm > kHadSmemBytes) return cudaErrorInvalidConfiguration;
   static bool attr_set[2] = {false, false};
   bool& done = attr_set[sizeof(R) == 4 ? 0 : 1];
   if (!done) {
-    // two CTAs per SM need <= 2 x 110 KB of shared memory
-    cudaError_t e = cudaFuncSetAttribute(hadamard_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
+    // two CTAs per SM
+    cudaError_t e = cudaFuncSetAttribute(hadamard_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kHadSmemBytes);
     if (e != cudaSuccess) return e;
     done = true;
   }
-  hadamard_kernel<R, TT><<<nwork, kHadThreads, sm, s>>>(tiles, work, src_ids, tgt_ids, pmap,
+  hadamard_kernel<R, TT><<<nwork, kHadThreads, sm, s>>>(groups, work, src_ids, tgt_ids, par_tab,
                                                        reinterpret_cast<const cplx<R>*>(spec),
                                                        reinterpret_cast<cplx<R>*>(acc), spec_blocks,
                                                        reinterpret_cast<const cplx<R>*>(kspec), kspec_level_stride);
@@ -266,47 +265,91 @@ template cudaError_t launch_hadamard_list<double>(int, const ListGroup*, int, in
                                                   const int*, const int*, const void*, void*, int, const void*,
                                                   size_t, cudaStream_t);
 
-template cudaError_t launch_hadamard<float>(int, const HadTile*, const HadWork*, int, int, const int*, const int*,
-                                            const int2*, const void*, void*, int, const void*, size_t, cudaStream_t);
-template cudaError_t launch_hadamard<double>(int, const HadTile*, const HadWork*, int, int, const int*, const int*,
-                                             const int2*, const void*, void*, int, const void*, size_t, cudaStream_t);
+template cudaError_t launch_hadamard<float>(int, const HadGroup*, const HadWork*, int, int, const int*, const int*,
+                                            const int16_t*, const void*, void*, int, const void*, size_t, cudaStream_t);
+template cudaError_t launch_hadamard<double>(int, const HadGroup*, const HadWork*, int, int, const int*, const int*,
+                                             const int16_t*, const void*, void*, int, const void*, size_t, cudaStream_t);
 
-void build_parent_map(const HadTile& tl, const int* src_slots, const int* tgt_slots, std::vector<int2>& out) {
-  const int np = tl.P[0] * tl.P[1] * tl.P[2];
-  const int NQ = tl.Rg[0] * tl.Rg[1] * tl.Rg[2];
-  std::vector<int2> m(np);
-  for (int pl = 0; pl < np; ++pl) {
-    const int pq[3] = {pl / (tl.P[1] * tl.P[2]), (pl / tl.P[2]) % tl.P[1], pl % tl.P[2]};
-    unsigned mask = 0;
-    bool has_tgt = false;  // a parent without targets does no work
-    for (int a = 0; a < 8; ++a) {
-      const int cell = ((2 * pq[0] + (a >> 2)) * 2 * tl.P[1] + (2 * pq[1] + ((a >> 1) & 1))) * 2 * tl.P[2] +
-                       (2 * pq[2] + (a & 1));
-      has_tgt |= tgt_slots[cell] >= 0;
-    }
-    if (!has_tgt) {
-      m[pl] = make_int2(pl, 0);
-      continue;
-    }
-    for (int e = 0; e < 27; ++e) {
-      if (tl.excl_near && e == 13) continue;
-      int n[3];
-      bool in = true;
-      for (int a = 0; a < 3; ++a) {
-        const int ea = (a == 0 ? e / 9 : a == 1 ? (e / 3) % 3 : e % 3) - 1;
-        n[a] = tl.p0[a] + pq[a] - tl.r0[a] + ea;
-        in &= n[a] >= 0 && n[a] < tl.Rg[a];
+// Shared memory of a group in 32-byte units: per chunk 8 slots per cell and
+// the 343 kernel spectra, plus the [27][nact] int16 neighbour table.
+static int group_units(int ncell, int nact, int cpc) { return (8 * ncell + kNOff) * cpc + (54 * nact + 31) / 32; }
+
+static int cell_key(const int* ch) {  // first child that is a source: identifies the cell
+  for (int b = 0; b < 8; ++b)
+    if (ch[b] >= 0) return ch[b];
+  return -1;
+}
+
+void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchunk, HadLists& L) {
+  const int max_units = (int)(kHadSmemBytes / 32);
+  size_t pos = 0;
+  while (pos < recs.size()) {
+    // take parents, in order, while the group's parents and cells fit
+    std::unordered_map<int, int> cell_of;  // cell key -> index in `cells`
+    std::vector<const int*> cells;         // the 8 children of each cell
+    std::vector<size_t> members;
+    while (pos < recs.size() && (int)members.size() < kHadMaxParents) {
+      const ParentRec& r = recs[pos];
+      int new_cells = 0;
+      for (int e = 0; e < 27; ++e) {
+        const int key = cell_key(r.cell[e]);
+        new_cells += key >= 0 && !cell_of.count(key);
       }
-      if (!in) continue;
-      const int q = (n[0] * tl.Rg[1] + n[1]) * tl.Rg[2] + n[2];
-      bool any = false;
-      for (int b = 0; b < 8; ++b) any |= src_slots[b * NQ + q] >= 0;
-      if (any) mask |= 1u << e;
+      if (!members.empty() &&
+          group_units((int)cells.size() + new_cells, (int)members.size() + 1, 1) > max_units)
+        break;
+      for (int e = 0; e < 27; ++e) {
+        const int key = cell_key(r.cell[e]);
+        if (key >= 0 && !cell_of.count(key)) {
+          cell_of.emplace(key, (int)cells.size());
+          cells.push_back(r.cell[e]);
+        }
+      }
+      members.push_back(pos++);
     }
-    m[pl] = make_int2(pl, (int)mask);
+    // cells in block-id order (block ids follow the level's coordinate order on
+    // the meshes built here), so that consecutive parents of a full tile see
+    // consecutive cells and the warp's shared-memory reads do not conflict
+    std::vector<int> order(cells.size());
+    for (size_t c = 0; c < order.size(); ++c) order[c] = (int)c;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return cell_key(cells[a]) < cell_key(cells[b]); });
+    std::vector<const int*> sorted(cells.size());
+    for (size_t c = 0; c < order.size(); ++c) {
+      sorted[c] = cells[order[c]];
+      cell_of[cell_key(sorted[c])] = (int)c;
+    }
+    cells.swap(sorted);
+
+    HadGroup gp;
+    gp.level = level;
+    gp.nact = (int)members.size();
+    gp.ncell = (int)cells.size();
+    gp.pslots = 1;
+    while (gp.pslots < gp.nact) gp.pslots <<= 1;
+    int cpc = std::min(kHadMaxCpc, kHadThreads / (gp.pslots * 2));
+    while (cpc > 1 && group_units(gp.ncell, gp.nact, cpc) > max_units) cpc >>= 1;
+    gp.cpc = cpc;
+    L.max_units = std::max(L.max_units, group_units(gp.ncell, gp.nact, cpc));
+    // sources: child b of cell c at slot b * ncell + c (-1: absent, zero spectrum)
+    gp.src_off = (int)L.src_ids.size();
+    for (int b = 0; b < 8; ++b)
+      for (int c = 0; c < gp.ncell; ++c) L.src_ids.push_back(cells[c][b]);
+    // per parent: the cell of each neighbour (e-major table) and the 8 targets
+    gp.par_off = (int)L.par_tab.size();
+    L.par_tab.resize(L.par_tab.size() + (size_t)27 * gp.nact, -1);
+    gp.tgt_off = (int)L.tgt_ids.size();
+    for (int m = 0; m < gp.nact; ++m) {
+      const ParentRec& r = recs[members[m]];
+      for (int e = 0; e < 27; ++e) {
+        const int key = cell_key(r.cell[e]);
+        if (key >= 0) L.par_tab[gp.par_off + e * gp.nact + m] = (int16_t)cell_of.at(key);
+      }
+      L.tgt_ids.insert(L.tgt_ids.end(), r.tgt, r.tgt + 8);
+    }
+    for (int c0 = 0; c0 < nchunk; c0 += cpc)
+      L.work.push_back(HadWork{(int)L.groups.size(), c0, std::min(cpc, nchunk - c0)});
+    L.groups.push_back(gp);
   }
-  // spatial order: consecutive threads read consecutive shared-memory vectors
-  out.insert(out.end(), m.begin(), m.end());
 }
 
 }  // namespace flgf

@@ -7,6 +7,8 @@
 
 #include <vector>
 
+#include "common.cuh"
+
 struct flgf_ctx;
 
 namespace flgf {
@@ -54,30 +56,47 @@ cudaError_t launch_kernel_spectra(int N, const double* karr, void* kspec_level, 
                                   cudaStream_t s);
 
 // ---- a3 spectrum multiply-accumulate (hadamard.cu) ------------------------
-struct HadTile {
-  int src_off;      // offset into the source id list: 8 * NQ slots, parity-major (slot = b * NQ + q)
-  int tgt_off;      // offset into tgt id array; (2 Px)(2 Py)(2 Pz) target cells, last axis fastest
-  int level;        // octree level k (selects the kernel spectra)
-  int excl_near;    // 1 when near neighbours are not part of this level's lists
-  int p0[3];        // tile parent box origin (parent coords)
-  int P[3];         // tile parent box dims
-  int r0[3];        // region parent box origin
-  int Rg[3];        // region parent box dims (NQ = Rg0 Rg1 Rg2)
-  int pslots;       // parent slots per chunk: power of two >= P0 P1 P2
-  int cpc;          // frequency chunks per CTA (pslots * groups * cpc = threads per CTA)
-  int pmap_off;     // offset into the parent map: per slot (parent index in the tile, 27-bit neighbour mask)
+// Dense MAC: groups of parents (see hadamard.cu).
+struct HadGroup {
+  int level;     // octree level k (selects the kernel spectra)
+  int nact;      // parents (<= kHadMaxParents)
+  int pslots;    // parent slots per (frequency group, chunk): power of two >= nact
+  int cpc;       // frequency chunks per CTA (pslots * 2 * cpc <= kHadThreads threads)
+  int ncell;     // neighbour cells that hold sources
+  int par_off;   // into the parent table: [27][nact] cell of neighbour e, or -1
+  int tgt_off;   // into the target list: [nact][8] spectrum column or -1 (child a = 4 a0 + 2 a1 + a2)
+  int src_off;   // into the source list: [8][ncell] spectrum column of child b of cell c, or -1
 };
-// Work item of the spectrum MAC: (tile, first chunk).
+// Work item of the dense MAC: (group, first chunk, chunks).
 struct HadWork {
-  int tile, chunk0, nch;
+  int group, chunk0, nch;
 };
+constexpr int kHadThreads = 256;              // threads per CTA
+constexpr int kHadMaxCpc = 4;                 // frequency chunks per CTA
+constexpr int kHadMaxParents = 128;           // parents per group
+constexpr size_t kHadSmemBytes = 110 * 1024;  // dynamic shared memory per CTA (two CTAs per SM)
+// One parent with targets: its 8 children (spectrum column or -1) and, per
+// neighbour e (e = 9 (e0+1) + 3 (e1+1) + (e2+1)), the 8 children of parent
+// p + e that are sources (all -1 when there are none or the pair is excluded).
+struct ParentRec {
+  int tgt[8];
+  int cell[27][8];
+};
+// Launch lists of the dense MAC, appended to by pack_parent_groups.
+struct HadLists {
+  std::vector<HadGroup> groups;
+  std::vector<HadWork> work;
+  std::vector<int> src_ids, tgt_ids;
+  std::vector<int16_t> par_tab;
+  int max_units = 0;  // max over groups of their shared memory in 32-byte units
+};
+// Packs parent records, in order, into groups of one octree level and their
+// work items (nchunk frequency chunks).
+void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchunk, HadLists& L);
 template <typename R>
-cudaError_t launch_hadamard(int N, const HadTile* tiles, const HadWork* work, int nwork, int max_units /* max (8 NQ + 343) cpc */,
-                            const int* src_ids, const int* tgt_ids, const int2* pmap, const void* spec, void* acc,
+cudaError_t launch_hadamard(int N, const HadGroup* groups, const HadWork* work, int nwork, int max_units,
+                            const int* src_ids, const int* tgt_ids, const int16_t* par_tab, const void* spec, void* acc,
                             int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s);
-// Parent map of one tile: per parent slot (spatial order) the mask of
-// neighbour parents e that lie in the region and hold at least one source.
-void build_parent_map(const HadTile& tl, const int* src_slots, const int* tgt_slots, std::vector<int2>& out);
 // Sparse tiles: explicit (target, source) pair lists.  A group holds up to
 // kListTargets existing targets of one tile (sorted by list length), the
 // union of their existing sources, and per target its pair entries
@@ -99,9 +118,6 @@ template <typename R>
 cudaError_t launch_hadamard_list(int N, const ListGroup* groups, int ngroups, int max_src, const int* tgt,
                                  const int* len, const int* ent, const int* src, const void* spec, void* acc,
                                  int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s);
-// Threads per CTA of the spectrum MAC, and the most frequency chunks one CTA takes.
-constexpr int kHadThreads = 256;
-constexpr int kHadMaxCpc = 4;
 
 // ---- a1/a5 and multi-resolution stencils (stencil.cu) ----------------------
 // J1: dense 1-D Lagrange matrix [2N][N] (row = child node of the two children, column = parent node).
