@@ -60,6 +60,72 @@ def torus(x, centre, R: float, sigma: float, axis_rot=None):
     return np.exp(-d2 / (2.0 * sigma * sigma))
 
 
+def vortex_ring(x, centre=(0.5, 0.5, 0.5), R: float = 0.125, c1: float = 1e3, c2: float = 10.0):
+    """Manufactured solution of Sec. 3.1 (Eqs. streamfunc, streamfunc_f): the
+    streamfunction Psi = f(sqrt((r - R)^2 + z^2) / R) e_theta of a vortex ring
+    of radius R about the z axis through ``centre``, with the bump
+    f(t) = c1 exp(-c2 / (1 - t^2)) for |t| < 1 and 0 elsewhere, and the
+    vorticity omega = Laplacian(Psi) evaluated analytically.
+
+    Returns the x components (psi_x, omega_x) at points x (..., 3); each
+    Cartesian component satisfies the scalar Poisson equation on its own.
+    For an azimuthal axisymmetric field psi(r, z) e_theta the Laplacian is
+    (d_rr + d_r / r + d_zz - 1 / r^2) psi e_theta; with psi = f(rho / R),
+    rho the distance to the core circle, d_rr + d_zz gives
+    f'' / R^2 + f' / (R rho), and d_r psi = f' (r - R) / (R rho).
+    """
+    d = np.asarray(x, dtype=np.float64) - np.asarray(centre, dtype=np.float64)
+    r = np.hypot(d[..., 0], d[..., 1])
+    rho = np.hypot(r - R, d[..., 2])
+    t = rho / R
+    inside = t < 1.0
+    ts = np.where(inside, t, 0.0)
+    s = 1.0 - ts * ts
+    f = np.where(inside, c1 * np.exp(-c2 / s), 0.0)
+    fp_over_rho = -2.0 * c2 * f / (s * s * R)               # f'(t) / rho, finite at rho = 0
+    fpp = -2.0 * c2 * f / (s * s) * (1.0 - 2.0 * c2 * ts * ts / (s * s) + 4.0 * ts * ts / s)
+    rs = np.where(inside, r, 1.0)                            # r > 0 on the support
+    omega_t = fpp / (R * R) + fp_over_rho / R + fp_over_rho * (rs - R) / (R * rs) - f / (rs * rs)
+    sin_t = np.where(inside, d[..., 1] / rs, 0.0)            # e_theta = (-sin, cos, 0)
+    return -f * sin_t, np.where(inside, -omega_t * sin_t, 0.0)
+
+
+def split_blocks(coords_levels):
+    """Global refinement with a fixed mesh topology: every block of every level
+    becomes its 8 children (same physical regions, half the spacing)."""
+    out = []
+    for c in coords_levels:
+        c = np.asarray(c, dtype=np.int64).reshape(-1, 3)
+        kids = (2 * c[:, None, :] + np.array(list(np.ndindex(2, 2, 2)))[None]).reshape(-1, 3)
+        out.append(kids[np.lexsort((kids[:, 2], kids[:, 1], kids[:, 0]))])
+    return out
+
+
+def config_vortex_ring(n_levels: int = 3, N: int = 8, nbase: int = 4, splits: int = 0, alpha: float = 1.0 / 32):
+    """Single vortex ring of Sec. 3.1 (c1 = 1e3, c2 = 10, R = 0.125, centred in the
+    unit cube) on nbase^3 base blocks.  Refinement reads Eq. ref_crit as: a
+    level-l block (l < n_levels - 1) is refined where |omega| exceeds
+    alpha^(n_levels - 1 - l) of its maximum on that level.  ``splits`` then
+    refines the whole mesh globally that many times with a fixed topology.
+    Returns (Problem, psi_x per level) with the source omega_x and the
+    analytic solution sampled at cell centres."""
+    h0 = 1.0 / (nbase * N)
+    thr = [alpha ** (n_levels - 1 - l) for l in range(n_levels - 1)]
+    prob = refine_mesh(lambda x: vortex_ring(x)[1], box_coords(nbase), N, h0, n_levels, thresholds=thr)
+    coords = prob.coords
+    for _ in range(splits):
+        coords = split_blocks(coords)
+        h0 = h0 / 2
+    out = Problem(N=N, h0=h0, name=f"vortex_ring_L{n_levels}_b{nbase}_s{splits}")
+    psi = []
+    for l, c in enumerate(coords):
+        p, w = vortex_ring(cell_centres(c, N, h0 / (1 << l)))
+        out.coords.append(c)
+        out.f.append(w)
+        psi.append(p)
+    return out, psi
+
+
 def truncate(f: np.ndarray, ref: float | None = None) -> np.ndarray:
     m = np.max(np.abs(f)) if ref is None else ref
     return np.where(np.abs(f) < TRUNC * m, 0.0, f)
@@ -142,11 +208,11 @@ def _nbrs26(c):
             yield (c[0] + e[0] - 1, c[1] + e[1] - 1, c[2] + e[2] - 1)
 
 
-def refine_mesh(src, base_coords, N: int, h0: float, n_levels: int, threshold: float = 1e-3):
+def refine_mesh(src, base_coords, N: int, h0: float, n_levels: int, threshold: float = 1e-3, thresholds=None):
     """Block-refined mesh for a source callable src(x) -> f (x: (..., 3) physical).
 
     A block of level l < n_levels-1 is refined when any of its cells has
-    |f| > threshold * max|f| on that level.  The mesh is then closed so that
+    |f| > threshold * max|f| on that level (``thresholds[l]`` when given).  The mesh is then closed so that
     every refined block has all 26 same-level neighbours (zero-source blocks
     are added where needed, refining coarser blocks if necessary) and every
     refined block has all 8 children.  Returns a Problem with sources sampled
@@ -159,7 +225,8 @@ def refine_mesh(src, base_coords, N: int, h0: float, n_levels: int, threshold: f
         cl = np.array(sorted(levels[l]), dtype=np.int64)
         vals = src(cell_centres(cl, N, h))
         m = np.max(np.abs(vals)) if vals.size else 0.0
-        hit = np.any(np.abs(vals) > threshold * m, axis=(1, 2, 3)) if m > 0 else np.zeros(len(cl), bool)
+        thr = threshold if thresholds is None else thresholds[l]
+        hit = np.any(np.abs(vals) > thr * m, axis=(1, 2, 3)) if m > 0 else np.zeros(len(cl), bool)
         refined[l] = set(map(tuple, cl[hit].tolist()))
         # close: neighbours of refined blocks exist on this level (add them,
         # and refine their parents on coarser levels as far as needed)
