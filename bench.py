@@ -202,6 +202,7 @@ def run_ours(a, rank, world, dist):
     import torch
 
     from paper_1911_10228_gb300 import flgf as F
+    from paper_1911_10228_gb300 import multirank as MR
     from paper_1911_10228_gb300.inputs import config_uniform_256
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
@@ -228,8 +229,7 @@ def run_ours(a, rank, world, dist):
         bs.stage_times(reset=True)
         steps = a.steps if prec == "fp32" else max(3, min(a.steps, 10))
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        if dist:
-            torch.distributed.barrier()
+        MR.barrier("cuda")
         torch.cuda.synchronize()
         sampler.start()
         for s0, s1 in evs:
@@ -240,16 +240,13 @@ def run_ours(a, rank, world, dist):
             s1.record(ctx.stream)
         torch.cuda.synchronize()
         sampler.stop()
-        if dist:
-            torch.distributed.barrier()
+        MR.barrier("cuda")
         step_ms = [s0.elapsed_time(s1) for s0, s1 in evs]
-        total = torch.tensor([sum(step_ms)], dtype=torch.float64, device="cuda")
-        if dist:
-            torch.distributed.all_reduce(total, op=torch.distributed.ReduceOp.MAX)
+        total = MR.all_max(sum(step_ms), "cuda")   # the slowest rank's time
         stage, n_timed = bs.stage_times(reset=True)
         bs.set_option(F.OPT_TIMING, 0)
         res[prec] = {
-            "ms_per_step": float(total.item()) / steps, "steps": steps, "launches": bs.launch_count(),
+            "ms_per_step": total / steps, "steps": steps, "launches": bs.launch_count(),
             "stages_ms": {k: v / max(n_timed, 1) for k, v in stage.items()},
             "work": bs.work_counts(), "ctx": ctx, "bs": bs,
         }
@@ -260,11 +257,16 @@ def run_ours(a, rank, world, dist):
     batched = None
     if not a.no_batched:
         from paper_1911_10228_gb300.inputs import config_batched
-        probs = config_batched()
-        bdof = sum(p.dof() for p in probs)
-        batched = {"workload": "64 random sparse problems (seeds 0-63), 16^3 blocks, block counts log-uniform "
-                               "in [8, 4096] over 1-3 levels, 1-4 Gaussians each, one block set, CUDA graph",
-                   "dof": bdof, "blocks": int(sum(len(c) for p in probs for c in p.coords))}
+        # each rank solves its own 64 problems (seeds 64 r .. 64 r + 63): no exchange between ranks
+        seeds = MR.problem_seeds(64, rank)
+        probs = config_batched(64, first_seed=seeds[0])
+        bdof_rank = sum(p.dof() for p in probs)
+        bdof = MR.all_sum(bdof_rank, "cuda")
+        batched = {"workload": "64 random sparse problems per GPU (seeds 64 r .. 64 r + 63 on rank r), 16^3 blocks, "
+                               "block counts log-uniform in [8, 4096] over 1-3 levels, 1-4 Gaussians each, one block "
+                               "set, CUDA graph",
+                   "dof": int(bdof), "dof_rank0": bdof_rank,
+                   "blocks_rank0": int(sum(len(c) for p in probs for c in p.coords))}
         outs = {}
         plan = None
         for prec in precs:
@@ -290,6 +292,8 @@ def run_ours(a, rank, world, dist):
             torch.cuda.synchronize()
             nb = a.steps if prec == "fp32" else 1
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb)]
+            MR.barrier("cuda")
+            torch.cuda.synchronize()
             sampler.start()
             for s0, s1 in ev:
                 with torch.cuda.stream(bctx.stream):
@@ -299,8 +303,9 @@ def run_ours(a, rank, world, dist):
                 s1.record(bctx.stream)
             torch.cuda.synchronize()
             sampler.stop()
-            ms = float(np.mean([s0.elapsed_time(s1) for s0, s1 in ev]))
-            batched[prec] = {"value": bdof * world / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "steps": nb,
+            MR.barrier("cuda")
+            ms = MR.all_max(float(np.mean([s0.elapsed_time(s1) for s0, s1 in ev])), "cuda")
+            batched[prec] = {"value": bdof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "steps": nb,
                              "launches_per_step": bbs.launch_count()}
             outs[prec] = [[bbs.potential(i, l) for l in range(p.n_levels)] for i, p in enumerate(probs)]
             bbs.close()
@@ -330,10 +335,8 @@ def run_ours(a, rank, world, dist):
         bs.potential_host(0, 0, out=h_out.numpy())
         if i >= a.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t))
-    e2e = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device="cuda")
-    if dist:
-        torch.distributed.all_reduce(e2e, op=torch.distributed.ReduceOp.MAX)
-    e2e_ms_step = float(e2e.item()) / a.steps if e2e_ms else None
+    e2e = MR.all_max(sum(e2e_ms), "cuda")
+    e2e_ms_step = e2e / a.steps if e2e_ms else None
     nbytes = h_src.numel() * 4
 
     # accuracy and CPU baseline against the FP64 oracle (rank 0, one GPU only)

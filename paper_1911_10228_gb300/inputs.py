@@ -373,7 +373,8 @@ def random_sparse_problem(seed: int, N: int = 16, nblk_range=(8, 4096), max_leve
     return p
 
 
-def config_batched(n_problems: int = 64, N: int = 16):
-    """64 independent problems (seeds 0..63): block counts log-uniform in [8, 4096]
-    over 1-3 levels, random disjoint sparse base sets, random Gaussian sources."""
-    return [random_sparse_problem(s, N=N) for s in range(n_problems)]
+def config_batched(n_problems: int = 64, N: int = 16, first_seed: int = 0):
+    """64 independent problems (seeds first_seed .. first_seed + 63): block counts
+    log-uniform in [8, 4096] over 1-3 levels, random disjoint sparse base sets,
+    random Gaussian sources."""
+    return [random_sparse_problem(s, N=N) for s in range(first_seed, first_seed + n_problems)]

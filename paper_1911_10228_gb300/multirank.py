@@ -1,0 +1,54 @@
+"""Host-side logic of multi-process runs (one process per GPU).
+
+The solver itself needs no exchange between GPUs for the workloads measured
+here: the uniform solve runs as independent replicas, and the batched form is
+a set of independent problems, so a job of ``world`` ranks gives each rank its
+own disjoint slice of problems.  What the ranks share is only bookkeeping:
+a barrier around the timed region, the maximum of the ranks' timings, and the
+sum of the work they did.  These helpers work with any initialised
+``torch.distributed`` backend (NCCL on GPUs, gloo on CPUs) and reduce to the
+plain value in a single-process run.
+"""
+from __future__ import annotations
+
+import torch
+import torch.distributed as dist
+
+
+def active() -> bool:
+    return dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+
+
+def _reduce(x: float, op, device) -> float:
+    if not active():
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
+def all_max(x: float, device="cpu") -> float:
+    """Maximum over ranks (the job's time is its slowest rank's)."""
+    return _reduce(x, dist.ReduceOp.MAX, device)
+
+
+def all_sum(x: float, device="cpu") -> float:
+    """Sum over ranks (the job's work is every rank's work)."""
+    return _reduce(x, dist.ReduceOp.SUM, device)
+
+
+def barrier(device=None):
+    if active():
+        if device is not None and torch.device(device).type == "cuda":
+            dist.barrier(device_ids=[torch.device(device).index or 0])
+        else:
+            dist.barrier()
+
+
+def problem_seeds(per_rank: int, rank: int) -> list[int]:
+    """Seeds of this rank's problems in a job of per_rank problems per rank:
+    rank r takes seeds [r * per_rank, (r + 1) * per_rank), so the ranks' slices
+    are disjoint, and rank 0 alone reproduces the single-GPU batch."""
+    if per_rank < 0 or rank < 0:
+        raise ValueError("per_rank and rank must be non-negative")
+    return list(range(rank * per_rank, (rank + 1) * per_rank))
