@@ -9,8 +9,12 @@
 //  a9  source correction:                        f^{l+1} -= L_Q^{(h_{l+1})} (J^l u~^l).
 //  a10 7-point Laplacian L_Q^{(h)} u = (sum of 6 neighbours - 6 u) / h^2.
 // All tensor-product operators are applied axis by axis in shared memory.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace flgf {
 
@@ -67,27 +71,45 @@ __device__ __forceinline__ void load_band(const double* __restrict__ J1, R* W) {
   }
 }
 
-// a1: parent += sum over existing children of (R_c0 x R_c1 x R_c2) child.
-// One thread per line; N^2 threads.  Axis-2 lines are contiguous (padded rows
-// keep them conflict-free), axis-1 and axis-0 lines are strided.
+// a1: parent = sum over existing children of (R_c0 x R_c1 x R_c2) child.
+// A cluster of 8 CTAs per parent, CTA rank c = child position (c0 c1 c2): each
+// CTA applies the three 1-D passes to its own child (one thread per line, N^2
+// threads; axis-2 lines are contiguous, padded rows keep the strided axis-1
+// and axis-0 lines conflict-free) and leaves the result in its shared memory;
+// after a cluster barrier CTA c sums slice c of the parent over the 8 CTAs'
+// shared memory (distributed shared memory, fixed order) and writes it.  The
+// 8 children of a parent are thus transformed at the same time, not one
+// after another, and nothing but the parent goes back to HBM.
 template <typename R, int N, int NI>
-__global__ void __launch_bounds__(N * N) anterp_kernel(const double* __restrict__ J1, const int* __restrict__ parents,
-                                                       const int* __restrict__ children, R* __restrict__ nodes) {
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(N * N)
+    anterp_kernel(const double* __restrict__ J1, const int* __restrict__ parents, const int* __restrict__ children,
+                  R* __restrict__ nodes) {
   constexpr int N3 = N * N * N, PS = N * N * (N + 1);
+  constexpr int V = 16 / (int)sizeof(R);  // values per 16-byte vector
+  constexpr int PER = N3 / V / (N * N);    // vectors per thread
+  static_assert(N % V == 0 && PER * V * N * N == N3, "whole vectors per thread");
   __shared__ R W[2 * N * NI];
-  __shared__ R A[PS];  // each thread transforms whole lines in place
+  __shared__ __align__(16) R A[PS];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int c = (int)cluster.block_rank();
+  const int pi = blockIdx.x / 8;
   load_band<R, N, NI>(J1, W);
   const int t = threadIdx.x, u = t / N, v = t % N;
+  const int cid = children[pi * 8 + c];
   R acc[N];
 #pragma unroll
   for (int q = 0; q < N; ++q) acc[q] = R(0);
-  for (int c = 0; c < 8; ++c) {
-    const int cid = children[blockIdx.x * 8 + c];
-    if (cid < 0) continue;
+  if (cid >= 0) {
     const int c0 = c >> 2, c1 = (c >> 1) & 1, c2 = c & 1;
-    __syncthreads();
-    const R* src = nodes + (size_t)cid * N3;
-    for (int i = t; i < N3; i += blockDim.x) A[pidx<N>(i / (N * N), (i / N) % N, i % N)] = src[i];
+    const int4* src = reinterpret_cast<const int4*>(nodes + (size_t)cid * N3);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int4 val = __ldg(src + t + p * N * N);
+      const int i = (t + p * N * N) * V;  // V consecutive values of one row
+      const R* pv = reinterpret_cast<const R*>(&val);
+#pragma unroll
+      for (int j = 0; j < V; ++j) A[pidx<N>(i / (N * N), (i / N) % N, i % N + j)] = pv[j];
+    }
     __syncthreads();
     R in[N], out[N];
     // axis 2: line (u, v) = A[u][v][:]
@@ -104,14 +126,26 @@ __global__ void __launch_bounds__(N * N) anterp_kernel(const double* __restrict_
 #pragma unroll
     for (int j = 0; j < N; ++j) A[pidx<N>(u, j, v)] = out[j];
     __syncthreads();
-    // axis 0: line (u, v) = A[:][u][v], accumulated in registers
+    // axis 0: line (u, v) = A[:][u][v]
 #pragma unroll
     for (int i = 0; i < N; ++i) in[i] = A[pidx<N>(i, u, v)];
     if (c0) line_anterp<R, N, NI, 1>(in, acc, W); else line_anterp<R, N, NI, 0>(in, acc, W);
+    __syncthreads();
   }
-  R* dst = nodes + (size_t)parents[blockIdx.x] * N3;
+  // this child's contribution, dense [i][u][v] (an absent child contributes zero)
 #pragma unroll
-  for (int i = 0; i < N; ++i) dst[(i * N + u) * N + v] = acc[i];
+  for (int i = 0; i < N; ++i) A[(i * N + u) * N + v] = acc[i];
+  cluster.sync();
+  // slice c of the parent: sum over the 8 CTAs in rank order
+  constexpr int SL = N3 / 8;
+  R* dst = nodes + (size_t)parents[pi] * N3;
+  for (int i = c * SL + t; i < (c + 1) * SL; i += N * N) {
+    R sum = R(0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sum += cluster.map_shared_rank(A, q)[i];
+    dst[i] = sum;
+  }
+  cluster.sync();  // no CTA leaves while others still read its shared memory
 }
 
 // a5: child += (J_c0 x J_c1 x J_c2) parent.
@@ -433,7 +467,7 @@ static cudaError_t set_smem(Kern k, size_t bytes) {
 
 template <typename R, int N, int NI>
 static cudaError_t anterp_n(const double* J1, const int* parents, const int* children, int n, R* nodes, cudaStream_t s) {
-  anterp_kernel<R, N, NI><<<n, N * N, 0, s>>>(J1, parents, children, nodes);
+  anterp_kernel<R, N, NI><<<8 * n, N * N, 0, s>>>(J1, parents, children, nodes);  // clusters of 8 CTAs
   return cudaGetLastError();
 }
 template <typename R, int N, int NI>
