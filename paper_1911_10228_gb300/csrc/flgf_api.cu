@@ -723,7 +723,8 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     }
     // dense MAC: parent groups of every octree level
     HadLists hl;
-    for (int k = 0; k < (int)dpool.size(); ++k) pack_parent_groups(k, dpool[k], nchunk, hl);
+    for (int k = 0; k < (int)dpool.size(); ++k)
+      pack_parent_groups(k, dpool[k], nchunk, had_kernel_units(ctx->prec == FLGF_FP64), hl);
     // pair-list groups: consecutive pool targets (spatially close, so their
     // source sets overlap) up to kListTargets targets or kListMaxSrc sources
     for (int k = 0; k < (int)lpool.size(); ++k) {

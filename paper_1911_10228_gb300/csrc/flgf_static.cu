@@ -123,7 +123,7 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
       }
   const int nchunk = cv.fp64 ? nchunks<double>(N) : nchunks<float>(N);
   HadLists hl;
-  pack_parent_groups(0, recs, nchunk, hl);
+  pack_parent_groups(0, recs, nchunk, had_kernel_units(cv.fp64), hl);
   std::vector<int> ids(nblk);
   for (int b = 0; b < nblk; ++b) ids[b] = b;
   std::vector<double> scales(nblk, h * h);

@@ -62,12 +62,27 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadGroup
   const int S = 8 * NC;  // slots per (chunk, group): child b of cell c at b * NC + c
 
   int4* Ks = Fs + (size_t)gp.cpc * NG * S;
-  constexpr int KV = kNOff * T * (int)sizeof(cplx<R>) / 16;  // 16-byte vectors per chunk
+  // FP64 uses the three-product form (see below): per (offset, group) 32 bytes
+  // holding kr, kr + ki, ki - kr and padding; FP32 keeps the complex values
+  constexpr bool G3 = sizeof(R) == 8;
+  constexpr int KV = (G3 ? 2 * kNOff * NG : kNOff * T * (int)sizeof(cplx<R>) / 16);  // 16-byte vectors per chunk
   int16_t* NB = reinterpret_cast<int16_t*>(Ks + (size_t)gp.cpc * KV);
   for (int i = tid; i < 27 * gp.nact; i += kHadThreads) NB[i] = par_tab[gp.par_off + i];
-  for (int i = tid; i < wk.nch * KV; i += kHadThreads) {
-    const int cs = i / KV, v = i % KV;
-    Ks[i] = __ldg(reinterpret_cast<const int4*>(kspec + (size_t)gp.level * kstride + (size_t)(wk.chunk0 + cs) * kNOff * T) + v);
+  if constexpr (G3) {
+    for (int i = tid; i < wk.nch * kNOff * T; i += kHadThreads) {
+      const int cs = i / (kNOff * T), d = (i / T) % kNOff, f = i % T;
+      const cplx<R> k = kspec[(size_t)gp.level * kstride + ((size_t)(wk.chunk0 + cs) * kNOff + d) * T + f];
+      R* dst = reinterpret_cast<R*>(Ks + (size_t)cs * KV + (size_t)(d * NG + f) * 2);
+      dst[0] = k.re;
+      dst[1] = k.re + k.im;
+      dst[2] = k.im - k.re;
+      dst[3] = R(0);
+    }
+  } else {
+    for (int i = tid; i < wk.nch * KV; i += kHadThreads) {
+      const int cs = i / KV, v = i % KV;
+      Ks[i] = __ldg(reinterpret_cast<const int4*>(kspec + (size_t)gp.level * kstride + (size_t)(wk.chunk0 + cs) * kNOff * T) + v);
+    }
   }
   for (int cs = 0; cs < wk.nch; ++cs) {
     int4* fdst = Fs + (size_t)cs * NG * S;
@@ -88,13 +103,22 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadGroup
   const int chunk = wk.chunk0 + cs;
   const int f0 = g * TT;
   const cplx<R>* Fg = reinterpret_cast<const cplx<R>*>(Fs + (size_t)(cs * NG + g) * S);
-  const cplx<R>* Kc = reinterpret_cast<const cplx<R>*>(Ks + (size_t)cs * KV) + f0;
+  const cplx<R>* Kc = reinterpret_cast<const cplx<R>*>(Ks + (size_t)cs * KV) + f0;  // complex form
+  const int4* Kg = Ks + (size_t)cs * KV + g * 2;                                      // three-product form
 
-  R ar[8][TT], ai[8][TT];
+  // FP32: ar, ai accumulate re and im with four FMAs per pair.  FP64 (bound by
+  // the FP64 FMA rate) takes the three-product form: with s = fr + fi,
+  // re(k f) = kr s - (kr + ki) fi and im(k f) = kr s + (ki - kr) fr, so the
+  // accumulators ar = sum kr s, ai = sum (kr + ki) fi, a3 = sum (ki - kr) fr
+  // take three FMAs per pair, and re = ar - ai, im = ar + a3.
+  R ar[8][TT], ai[8][TT], a3[8][G3 ? TT : 1];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int t = 0; t < TT; ++t) { ar[a][t] = R(0); ai[a][t] = R(0); }
+    for (int t = 0; t < TT; ++t) {
+      ar[a][t] = R(0); ai[a][t] = R(0);
+      if constexpr (G3) a3[a][t] = R(0);
+    }
 
   int cn = NB[slot];  // the next neighbour's cell is read one iteration ahead
   for (int e = 0; e < 27; ++e) {
@@ -104,34 +128,52 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadGroup
     const int e0 = e / 9 - 1, e1 = (e / 3) % 3 - 1, e2 = e % 3 - 1;
     // the 8 children b of neighbour parent p + e, TT frequencies each (zero where absent)
     const cplx<R>* fb = Fg + (size_t)c * TT;
-    R fr[8][TT], fi[8][TT];
+    R fr[8][TT], fi[8][TT], fs[8][G3 ? TT : 1];
 #pragma unroll
     for (int b = 0; b < 8; ++b)
 #pragma unroll
       for (int t = 0; t < TT; ++t) {
         const cplx<R> v = fb[(size_t)b * NC * TT + t];
         fr[b][t] = v.re; fi[b][t] = v.im;
+        if constexpr (G3) fs[b][t] = v.re + v.im;
       }
     // d = a - b - 2e takes 27 values delta - 2e (delta = a - b in {-1,0,1}^3):
     // one kernel-spectrum load per delta, applied to every (a, b) pair with a - b = delta
-    const cplx<R>* kb = Kc + (size_t)off_index(-2 * e0, -2 * e1, -2 * e2) * T;
+    const int eoff = off_index(-2 * e0, -2 * e1, -2 * e2);
 #pragma unroll
     for (int dl = 0; dl < 27; ++dl) {
       const int l0 = dl / 9 - 1, l1 = (dl / 3) % 3 - 1, l2 = dl % 3 - 1;
-      const int4 kv = *reinterpret_cast<const int4*>(kb + (l0 * 49 + l1 * 7 + l2) * T);
-      const cplx<R>* kk = reinterpret_cast<const cplx<R>*>(&kv);
+      const int d = eoff + l0 * 49 + l1 * 7 + l2;
+      if constexpr (G3) {
+        const int4* kp = Kg + (size_t)d * NG * 2;
+        const int4 kv0 = kp[0], kv1 = kp[1];
+        const R k0 = reinterpret_cast<const R*>(&kv0)[0], k1 = reinterpret_cast<const R*>(&kv0)[1];
+        const R k2 = reinterpret_cast<const R*>(&kv1)[0];
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int b0 = (a >> 2) - l0, b1 = ((a >> 1) & 1) - l1, b2 = (a & 1) - l2;
-        if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b2 < 0 || b2 > 1) continue;  // resolved at compile time
-        const int b = (b0 << 2) | (b1 << 1) | b2;
+        for (int a = 0; a < 8; ++a) {
+          const int b0 = (a >> 2) - l0, b1 = ((a >> 1) & 1) - l1, b2 = (a & 1) - l2;
+          if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b2 < 0 || b2 > 1) continue;  // resolved at compile time
+          const int b = (b0 << 2) | (b1 << 1) | b2;
+          ar[a][0] = fma(k0, fs[b][0], ar[a][0]);
+          ai[a][0] = fma(k1, fi[b][0], ai[a][0]);
+          a3[a][0] = fma(k2, fr[b][0], a3[a][0]);
+        }
+      } else {
+        const int4 kv = *reinterpret_cast<const int4*>(Kc + (size_t)d * T);
+        const cplx<R>* kk = reinterpret_cast<const cplx<R>*>(&kv);
 #pragma unroll
-        for (int t = 0; t < TT; ++t) {
-          const cplx<R> k = kk[t];
-          ar[a][t] = fma(k.re, fr[b][t], ar[a][t]);
-          ar[a][t] = fma(-k.im, fi[b][t], ar[a][t]);
-          ai[a][t] = fma(k.re, fi[b][t], ai[a][t]);
-          ai[a][t] = fma(k.im, fr[b][t], ai[a][t]);
+        for (int a = 0; a < 8; ++a) {
+          const int b0 = (a >> 2) - l0, b1 = ((a >> 1) & 1) - l1, b2 = (a & 1) - l2;
+          if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b2 < 0 || b2 > 1) continue;  // resolved at compile time
+          const int b = (b0 << 2) | (b1 << 1) | b2;
+#pragma unroll
+          for (int t = 0; t < TT; ++t) {
+            const cplx<R> k = kk[t];
+            ar[a][t] = fma(k.re, fr[b][t], ar[a][t]);
+            ar[a][t] = fma(-k.im, fi[b][t], ar[a][t]);
+            ai[a][t] = fma(k.re, fi[b][t], ai[a][t]);
+            ai[a][t] = fma(k.im, fr[b][t], ai[a][t]);
+          }
         }
       }
     }
@@ -144,7 +186,10 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadGroup
     if (sid < 0) continue;
     cplx<R>* o = acc + chunk_offset<R>(chunk, sid, spec_blocks) + f0;
 #pragma unroll
-    for (int t = 0; t < TT; ++t) o[t] = cplx<R>{ar[a][t], ai[a][t]};
+    for (int t = 0; t < TT; ++t) {
+      if constexpr (G3) o[t] = cplx<R>{ar[a][t] - ai[a][t], ar[a][t] + a3[a][t]};
+      else o[t] = cplx<R>{ar[a][t], ai[a][t]};
+    }
   }
 }
 
@@ -158,15 +203,10 @@ cudaError_t launch_hadamard(int N, const HadGroup* groups, const HadWork* work, 
   // neighbour table: max_units 32-byte units
   const size_t sm = 32 * (size_t)max_units;
   if (sm > kHadSmemBytes) return cudaErrorInvalidConfiguration;
-  static bool attr_set[2] = {false, false};
-  bool& done = attr_set[sizeof(R) == 4 ? 0 : 1];
-  if (!done) {
-    // two CTAs per SM
-    cudaError_t e = cudaFuncSetAttribute(hadamard_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kHadSmemBytes);
-    if (e != cudaSuccess) return e;
-    done = true;
-  }
+  // per device and cheap, so set on every launch (two CTAs per SM)
+  cudaError_t e = cudaFuncSetAttribute(hadamard_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kHadSmemBytes);
+  if (e != cudaSuccess) return e;
   hadamard_kernel<R, TT><<<nwork, kHadThreads, sm, s>>>(groups, work, src_ids, tgt_ids, par_tab,
                                                        reinterpret_cast<const cplx<R>*>(spec),
                                                        reinterpret_cast<cplx<R>*>(acc), spec_blocks,
@@ -243,14 +283,9 @@ cudaError_t launch_hadamard_list(int N, const ListGroup* groups, int ngroups, in
   constexpr int TT = (sizeof(R) == 4) ? 2 : 1;
   const size_t sm = sizeof(cplx<R>) * T * ((size_t)kNOff + max_src);
   if (sm > 200 * 1024) return cudaErrorInvalidConfiguration;
-  static bool attr_set[2] = {false, false};
-  bool& done = attr_set[sizeof(R) == 4 ? 0 : 1];
-  if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(hadamard_list_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e != cudaSuccess) return e;
-    done = true;
-  }
+  cudaError_t e = cudaFuncSetAttribute(hadamard_list_kernel<R, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  if (e != cudaSuccess) return e;
   dim3 grid(ngroups, nchunks<R>(N));
   hadamard_list_kernel<R, TT><<<grid, kListTargets * 2, sm, s>>>(
       groups, tgt, len, ent, src, reinterpret_cast<const cplx<R>*>(spec), reinterpret_cast<cplx<R>*>(acc),
@@ -272,7 +307,9 @@ template cudaError_t launch_hadamard<double>(int, const HadGroup*, const HadWork
 
 // Shared memory of a group in 32-byte units: per chunk 8 slots per cell and
 // the 343 kernel spectra, plus the [27][nact] int16 neighbour table.
-static int group_units(int ncell, int nact, int cpc) { return (8 * ncell + kNOff) * cpc + (54 * nact + 31) / 32; }
+static int group_units(int ncell, int nact, int cpc, int kunits) {
+  return (8 * ncell + kunits) * cpc + (54 * nact + 31) / 32;
+}
 
 static int cell_key(const int* ch) {  // first child that is a source: identifies the cell
   for (int b = 0; b < 8; ++b)
@@ -280,7 +317,7 @@ static int cell_key(const int* ch) {  // first child that is a source: identifie
   return -1;
 }
 
-void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchunk, HadLists& L) {
+void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchunk, int kunits, HadLists& L) {
   const int max_units = (int)(kHadSmemBytes / 32);
   size_t pos = 0;
   while (pos < recs.size()) {
@@ -296,7 +333,7 @@ void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchun
         new_cells += key >= 0 && !cell_of.count(key);
       }
       if (!members.empty() &&
-          group_units((int)cells.size() + new_cells, (int)members.size() + 1, 1) > max_units)
+          group_units((int)cells.size() + new_cells, (int)members.size() + 1, 1, kunits) > max_units)
         break;
       for (int e = 0; e < 27; ++e) {
         const int key = cell_key(r.cell[e]);
@@ -327,9 +364,9 @@ void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchun
     gp.pslots = 1;
     while (gp.pslots < gp.nact) gp.pslots <<= 1;
     int cpc = std::min(kHadMaxCpc, kHadThreads / (gp.pslots * 2));
-    while (cpc > 1 && group_units(gp.ncell, gp.nact, cpc) > max_units) cpc >>= 1;
+    while (cpc > 1 && group_units(gp.ncell, gp.nact, cpc, kunits) > max_units) cpc >>= 1;
     gp.cpc = cpc;
-    L.max_units = std::max(L.max_units, group_units(gp.ncell, gp.nact, cpc));
+    L.max_units = std::max(L.max_units, group_units(gp.ncell, gp.nact, cpc, kunits));
     // sources: child b of cell c at slot b * ncell + c (-1: absent, zero spectrum)
     gp.src_off = (int)L.src_ids.size();
     for (int b = 0; b < 8; ++b)

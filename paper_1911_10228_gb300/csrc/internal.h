@@ -91,8 +91,12 @@ struct HadLists {
   int max_units = 0;  // max over groups of their shared memory in 32-byte units
 };
 // Packs parent records, in order, into groups of one octree level and their
-// work items (nchunk frequency chunks).
-void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchunk, HadLists& L);
+// work items (nchunk frequency chunks); kunits = 32-byte units of kernel
+// spectra per chunk in shared memory (had_kernel_units).
+void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchunk, int kunits, HadLists& L);
+// Kernel-spectrum shared memory per chunk of the dense MAC, in 32-byte units:
+// the complex values (FP32) or the three-product form (FP64, twice as large).
+constexpr int had_kernel_units(bool fp64) { return fp64 ? 2 * kNOff : kNOff; }
 template <typename R>
 cudaError_t launch_hadamard(int N, const HadGroup* groups, const HadWork* work, int nwork, int max_units,
                             const int* src_ids, const int* tgt_ids, const int16_t* par_tab, const void* spec, void* acc,
