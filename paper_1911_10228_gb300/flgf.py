@@ -349,3 +349,25 @@ def solve_problem(ctx: Context, prob, correction: bool = True) -> list:
     torch.cuda.synchronize(ctx.device)
     bs.close()
     return out
+
+
+def solve_vector(ctx: Context, coords_levels, h0: float, components, correction: bool = True) -> list:
+    """Vector Poisson problem (each Cartesian component of a field, e.g. the
+    streamfunction of a vorticity field, is a scalar problem on the same mesh):
+    all components run as problems of one block set, so every stage of every
+    component shares the same kernel launches and the same cached kernel
+    spectra.  components[c][l] is component c's source on level l; returns the
+    potentials as components[c][l] device tensors."""
+    bs = BlockSet(ctx, [coords_levels] * len(components), [h0] * len(components))
+    try:
+        if not correction:
+            bs.set_option(OPT_CORRECTION, 0)
+        for c, levels in enumerate(components):
+            for l, f in enumerate(levels):
+                bs.load_source(c, l, torch.as_tensor(f))
+        bs.solve()
+        out = [[bs.potential(c, l) for l in range(len(coords_levels))] for c in range(len(components))]
+        torch.cuda.synchronize(ctx.device)
+        return out
+    finally:
+        bs.close()

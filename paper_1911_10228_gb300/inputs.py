@@ -60,6 +60,26 @@ def torus(x, centre, R: float, sigma: float, axis_rot=None):
     return np.exp(-d2 / (2.0 * sigma * sigma))
 
 
+def _vortex_ring_parts(x, centre, R, c1, c2):
+    """Bump value f, azimuthal vorticity omega_theta and (sin, cos) of the
+    azimuth at points x (..., 3); all zero outside the ring's support."""
+    d = np.asarray(x, dtype=np.float64) - np.asarray(centre, dtype=np.float64)
+    r = np.hypot(d[..., 0], d[..., 1])
+    rho = np.hypot(r - R, d[..., 2])
+    t = rho / R
+    inside = t < 1.0
+    ts = np.where(inside, t, 0.0)
+    s = 1.0 - ts * ts
+    f = np.where(inside, c1 * np.exp(-c2 / s), 0.0)
+    fp_over_rho = -2.0 * c2 * f / (s * s * R)               # f'(t) / rho, finite at rho = 0
+    fpp = -2.0 * c2 * f / (s * s) * (1.0 - 2.0 * c2 * ts * ts / (s * s) + 4.0 * ts * ts / s)
+    rs = np.where(inside, r, 1.0)                            # r > 0 on the support
+    omega_t = fpp / (R * R) + fp_over_rho / R + fp_over_rho * (rs - R) / (R * rs) - f / (rs * rs)
+    sin_t = np.where(inside, d[..., 1] / rs, 0.0)
+    cos_t = np.where(inside, d[..., 0] / rs, 0.0)
+    return f, np.where(inside, omega_t, 0.0), sin_t, cos_t
+
+
 def vortex_ring(x, centre=(0.5, 0.5, 0.5), R: float = 0.125, c1: float = 1e3, c2: float = 10.0):
     """Manufactured solution of Sec. 3.1 (Eqs. streamfunc, streamfunc_f): the
     streamfunction Psi = f(sqrt((r - R)^2 + z^2) / R) e_theta of a vortex ring
@@ -74,20 +94,16 @@ def vortex_ring(x, centre=(0.5, 0.5, 0.5), R: float = 0.125, c1: float = 1e3, c2
     rho the distance to the core circle, d_rr + d_zz gives
     f'' / R^2 + f' / (R rho), and d_r psi = f' (r - R) / (R rho).
     """
-    d = np.asarray(x, dtype=np.float64) - np.asarray(centre, dtype=np.float64)
-    r = np.hypot(d[..., 0], d[..., 1])
-    rho = np.hypot(r - R, d[..., 2])
-    t = rho / R
-    inside = t < 1.0
-    ts = np.where(inside, t, 0.0)
-    s = 1.0 - ts * ts
-    f = np.where(inside, c1 * np.exp(-c2 / s), 0.0)
-    fp_over_rho = -2.0 * c2 * f / (s * s * R)               # f'(t) / rho, finite at rho = 0
-    fpp = -2.0 * c2 * f / (s * s) * (1.0 - 2.0 * c2 * ts * ts / (s * s) + 4.0 * ts * ts / s)
-    rs = np.where(inside, r, 1.0)                            # r > 0 on the support
-    omega_t = fpp / (R * R) + fp_over_rho / R + fp_over_rho * (rs - R) / (R * rs) - f / (rs * rs)
-    sin_t = np.where(inside, d[..., 1] / rs, 0.0)            # e_theta = (-sin, cos, 0)
-    return -f * sin_t, np.where(inside, -omega_t * sin_t, 0.0)
+    f, w, sin_t, _ = _vortex_ring_parts(x, centre, R, c1, c2)
+    return -f * sin_t, -w * sin_t                            # e_theta = (-sin, cos, 0)
+
+
+def vortex_ring_vector(x, centre=(0.5, 0.5, 0.5), R: float = 0.125, c1: float = 1e3, c2: float = 10.0):
+    """All three Cartesian components of the vortex ring's streamfunction and
+    vorticity (see vortex_ring): arrays (..., 3), the z components zero."""
+    f, w, sin_t, cos_t = _vortex_ring_parts(x, centre, R, c1, c2)
+    z = np.zeros_like(f)
+    return np.stack([-f * sin_t, f * cos_t, z], axis=-1), np.stack([-w * sin_t, w * cos_t, z], axis=-1)
 
 
 def split_blocks(coords_levels):

@@ -3,7 +3,7 @@ streamfunc_f): the analytic vorticity omega = Laplacian(Psi) used as the source
 must be the Laplacian of the analytic streamfunction used as the answer."""
 import numpy as np
 
-from paper_1911_10228_gb300.inputs import config_vortex_ring, split_blocks, vortex_ring
+from paper_1911_10228_gb300.inputs import config_vortex_ring, split_blocks, vortex_ring, vortex_ring_vector
 
 C = np.array([0.5, 0.5, 0.5])
 R = 0.125
@@ -67,3 +67,30 @@ def test_global_split_keeps_the_topology():
         kids = {tuple(x) for x in q.coords[l + 1].tolist()}
         for c in q.coords[l][~leaf[l]]:
             assert all((2 * c[0] + i, 2 * c[1] + j, 2 * c[2] + k) in kids for i, j, k in np.ndindex(2, 2, 2))
+
+
+def test_vector_components():
+    """The y component is the x component rotated by 90 degrees about the ring
+    axis, its vorticity is its Laplacian, and the field is divergence-free."""
+    pts = _points(150, seed=2)
+    psi, w = vortex_ring_vector(pts)
+    assert np.array_equal(psi[:, 0], vortex_ring(pts)[0]) and np.all(psi[:, 2] == 0) and np.all(w[:, 2] == 0)
+    rot = pts.copy()                                    # (x, y) -> (y', -x') about the axis
+    d = pts - C
+    rot[:, 0], rot[:, 1] = C[0] - d[:, 1], C[1] + d[:, 0]
+    psi_rot = vortex_ring_vector(rot)[0]              # Psi(R p) = R Psi(p), R (vx, vy) = (-vy, vx)
+    assert np.allclose(psi_rot[:, 1], psi[:, 0], rtol=1e-10, atol=1e-12 * np.max(np.abs(psi)))
+    assert np.allclose(psi_rot[:, 0], -psi[:, 1], rtol=1e-10, atol=1e-12 * np.max(np.abs(psi)))
+    lap = _fd_laplacian(lambda q: vortex_ring_vector(q)[0][:, 1], pts, 1e-3)
+    assert np.max(np.abs(lap - w[:, 1])) < 1e-6 * np.max(np.abs(w[:, 1]))
+    h = 1e-3                                            # fourth-order first derivatives
+    div = np.zeros(len(pts))
+    size = np.zeros(len(pts))
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        g = lambda q: vortex_ring_vector(q)[0][:, a]
+        da = (-g(pts + 2 * e) + 8 * g(pts + e) - 8 * g(pts - e) + g(pts - 2 * e)) / (12 * h)
+        div += da
+        size += np.abs(da)
+    assert np.max(np.abs(div)) < 1e-6 * np.max(size)
