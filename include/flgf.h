@@ -201,7 +201,8 @@ int flgf_work_counts(const flgf_blockset* bs, int64_t* pairs, int64_t* fwd_ffts,
  * cudaMalloc's implicit synchronisation, processes whose device memory is
  * reserved up front).
  *   coords  host array [nblk][3] of block coordinates
- *   f, u    DEVICE arrays [nblk][N][N][N] in the context precision (borrowed)
+ *   f, u    DEVICE arrays [nblk][N][N][N] in the context precision (borrowed),
+ *           16-byte aligned
  *   h       lattice spacing (> 0)
  * Scratch: the spectra and launch lists live in a fixed ~18 MB array in
  * device memory that the library declares statically; every GPU that loads

@@ -78,6 +78,8 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
   };
   if (nblk < 1 || nblk > kStaticMaxBlocks || !coords || !f || !u || !(h > 0.0))
     return bad(FLGF_EINVAL, "convolve_static: need 1..32 blocks, coordinates, device f and u, h > 0");
+  if (reinterpret_cast<uintptr_t>(f) % 16 || reinterpret_cast<uintptr_t>(u) % 16)
+    return bad(FLGF_EINVAL, "convolve_static: f and u must be 16-byte aligned");
   const int N = cv.N;
   // one octree level: the parents of all blocks lie within one block of each other
   std::array<int, 3> plo = {INT32_MAX, INT32_MAX, INT32_MAX}, phi = {INT32_MIN, INT32_MIN, INT32_MIN};
