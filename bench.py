@@ -327,14 +327,28 @@ def run_ours(a, rank, world, dist):
     h_src = torch.empty(tuple(f64.shape), dtype=torch.float32, pin_memory=True)
     h_src.copy_(f64.float())
     h_out = torch.empty_like(h_src, pin_memory=True)
-    e2e_ms = []
-    for i in range(0 if a.no_e2e else a.warmup + a.steps):
-        t = time.perf_counter()
+    # Pipelined as a time-stepping caller would run it: the next step's source
+    # is loaded (host to device, on the library's copy stream) while the
+    # current solve runs, then the current potential is read back (device to
+    # host) and the next solve is enqueued.  Every step still moves its whole
+    # input in and its whole result out; the wall time covers them all.
+    def e2e_run(n):
         bs.load_source(0, 0, h_src)
         bs.solve()
-        bs.potential_host(0, 0, out=h_out.numpy())
-        if i >= a.warmup:
-            e2e_ms.append(1e3 * (time.perf_counter() - t))
+        for i in range(n):
+            if i + 1 < n:
+                bs.load_source(0, 0, h_src)
+            bs.potential_host(0, 0, out=h_out.numpy())
+            if i + 1 < n:
+                bs.solve()
+
+    e2e_ms = []
+    if not a.no_e2e:
+        e2e_run(a.warmup)
+        MR.barrier("cuda")
+        t = time.perf_counter()
+        e2e_run(a.steps)
+        e2e_ms.append(1e3 * (time.perf_counter() - t))
     e2e = MR.all_max(sum(e2e_ms), "cuda")
     e2e_ms_step = e2e / a.steps if e2e_ms else None
     nbytes = h_src.numel() * 4
@@ -415,7 +429,8 @@ def run_ours(a, rank, world, dist):
         "cpu_baseline": cpu,
         "e2e": None if e2e_ms_step is None else {
             "value": dof * world / (e2e_ms_step / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms_step},
+            "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms_step,
+            "note": "pinned host buffers; the next step's source load overlaps the current solve"},
         "gpu_launches": res["fp32"]["launches"] * a.steps,
         "clocks": sampler.summary(),
     }

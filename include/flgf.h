@@ -139,7 +139,14 @@ int64_t flgf_blockset_dof(const flgf_blockset* bs);
 
 /* Copy the source of (problem, level) from f ([nblk][N][N][N], context
  * precision).  Values on non-leaf blocks are ignored (they are replaced by the
- * coarsened finer source, Sec. 3 step 1). */
+ * coarsened finer source, Sec. 3 step 1).
+ * where = FLGF_HOST: the copy runs on the block set's own copy stream once the
+ * last flgf_solve has taken its copy of the sources, so it overlaps the rest
+ * of that solve; the call returns when the copy is done (f may be reused) and
+ * the next flgf_solve waits for it.  A time-stepping caller can thus load
+ * step i+1 before reading step i's potential.
+ * where = FLGF_DEVICE: the copy is enqueued on the context stream (f must stay
+ * valid until the next solve has run). */
 int flgf_load_source(flgf_blockset* bs, int problem, int level, const void* f, int where);
 
 /* Solve every problem of the block set (Sec. 3 algorithm; with one level it is

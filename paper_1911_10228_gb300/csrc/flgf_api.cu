@@ -185,6 +185,12 @@ struct flgf_blockset {
   void* lap_in = nullptr;
   void* lap_out = nullptr;
   int* d_err = nullptr;
+  // host source loads run on their own stream: they wait only until the
+  // solve in flight has copied the source buffer (ev_fuser_free), so they
+  // overlap the rest of that solve; the next solve waits for ev_loaded
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t ev_fuser_free = nullptr, ev_loaded = nullptr, ev_dev_load = nullptr;
+  bool load_pending = false;
   bool correction = true, solved = false;
   bool use_graph = false, timing = false;
   cudaGraphExec_t gexec = nullptr;
@@ -394,6 +400,10 @@ extern "C" void flgf_blockset_destroy(flgf_blockset* bs) {
   cudaFree(bs->lap_in);
   cudaFree(bs->lap_out);
   cudaFree(bs->d_err);
+  if (bs->ev_fuser_free) cudaEventDestroy(bs->ev_fuser_free);
+  if (bs->ev_loaded) cudaEventDestroy(bs->ev_loaded);
+  if (bs->ev_dev_load) cudaEventDestroy(bs->ev_dev_load);
+  if (bs->cstream) cudaStreamDestroy(bs->cstream);
   delete bs;
 }
 
@@ -1046,6 +1056,10 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
   if (e == cudaSuccess) e = cudaMemset(bs->fuser, 0, rs * N3 * bs->B);
   if (e == cudaSuccess) e = cudaMemset(bs->unodes, 0, rs * N3 * bs->G);
   if (e == cudaSuccess) e = cudaMemset(bs->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs->cstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->ev_fuser_free, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->ev_loaded, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->ev_dev_load, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? FLGF_ENOMEM : FLGF_ECUDA;
     return bail(code, std::string("blockset allocation: ") + cudaGetErrorString(e));
@@ -1088,8 +1102,22 @@ extern "C" int flgf_load_source(flgf_blockset* bs, int problem, int level, const
   if (check_pl(bs, problem, level) != FLGF_OK) return fail(ctx, FLGF_EINVAL, "load_source: bad problem/level");
   const LevelInfo& L = bs->prob[problem].lev[level];
   const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4, N3 = (size_t)ctx->N * ctx->N * ctx->N;
-  CK(cudaMemcpyAsync((char*)bs->fuser + rs * N3 * L.fw0, f, rs * N3 * L.c.size(), kind(where, true), ctx->stream));
-  if (where == FLGF_HOST) CK(cudaStreamSynchronize(ctx->stream));
+  char* dst = (char*)bs->fuser + rs * N3 * L.fw0;
+  const size_t bytes = rs * N3 * L.c.size();
+  if (where == FLGF_HOST) {
+    // on the copy stream, after the last solve has taken its copy of the source
+    // buffer and after earlier device loads; returns once the copy is done
+    CK(cudaStreamWaitEvent(bs->cstream, bs->ev_fuser_free, 0));
+    CK(cudaStreamWaitEvent(bs->cstream, bs->ev_dev_load, 0));
+    CK(cudaMemcpyAsync(dst, f, bytes, cudaMemcpyHostToDevice, bs->cstream));
+    CK(cudaEventRecord(bs->ev_loaded, bs->cstream));
+    CK(cudaEventSynchronize(bs->ev_loaded));
+    bs->load_pending = true;
+  } else {
+    if (bs->load_pending) CK(cudaStreamWaitEvent(ctx->stream, bs->ev_loaded, 0));
+    CK(cudaMemcpyAsync(dst, f, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaEventRecord(bs->ev_dev_load, ctx->stream));
+  }
   return FLGF_OK;
 }
 
@@ -1262,6 +1290,7 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
   } while (0)
   bs->launches = 0;
   RUN(cudaMemcpyAsync(fwork, bs->fuser, sizeof(R) * N3 * bs->B, cudaMemcpyDeviceToDevice, s));
+  RUN(cudaEventRecordWithFlags(bs->ev_fuser_free, s, bs->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   {
     StageScope sc(bs, 0);
     for (int l = bs->Lmax - 2; l >= 0; --l) {
@@ -1368,6 +1397,10 @@ extern "C" int flgf_solve(flgf_blockset* bs) {
   flgf_ctx* ctx = bs->ctx;
   collect_times(bs);
   cudaError_t e;
+  if (bs->load_pending) {  // a host load on the copy stream feeds this solve
+    CK(cudaStreamWaitEvent(ctx->stream, bs->ev_loaded, 0));
+    bs->load_pending = false;
+  }
   if (bs->use_graph) {
     if (!bs->gexec) {
       bs->ev_used = 0;
