@@ -97,3 +97,35 @@ def test_torus_multires_laplacian_consistency_and_fp32():
     bs.close()
     c64.close()
     c32.close()
+
+
+def test_batched_full_size_sampled_problems_match_oracle():
+    """The 64-problem batch (16^3 blocks, 1-3 levels) in the launch configuration
+    bench.py times, with the plan the autotuner picks on it: the smallest
+    one-, two- and three-level problems of the solved batch against the
+    oracle's multi-resolution solve."""
+    from oracle.multires import multires_solve
+    from paper_1911_10228_gb300.inputs import config_batched
+
+    probs = config_batched()
+    size = lambda i: sum(len(c) for c in probs[i].coords)
+    small = [min((i for i in range(len(probs)) if probs[i].n_levels == L), key=size) for L in (1, 2, 3)]
+    refs = {i: multires_solve(LGF(), probs[i].coords, probs[i].f, 16, 6, probs[i].h0) for i in small}
+    for precision, tol in (("fp64", 1e-10), ("fp32", 1e-4)):
+        ctx = F.Context(N=16, n_interp=6, precision=precision)
+        ctx.set_plan(list_pct=30, tile=(4, 4, 4))
+        bs = F.BlockSet(ctx, [p.coords for p in probs], [p.h0 for p in probs])
+        for i, p in enumerate(probs):
+            for l, f in enumerate(p.f):
+                bs.load_source(i, l, torch.as_tensor(f))
+        bs.set_option(F.OPT_GRAPH, 1)
+        bs.solve()
+        for i in small:
+            ref, leaf = refs[i]
+            scale = max(np.max(np.abs(r[m])) for r, m in zip(ref, leaf) if m.any())
+            for l in range(probs[i].n_levels):
+                u = bs.potential(i, l).double().cpu().numpy()
+                err = np.max(np.abs(u[leaf[l]] - ref[l][leaf[l]])) / scale if leaf[l].any() else 0.0
+                assert err < tol, (precision, i, l, err)
+        bs.close()
+        ctx.close()
