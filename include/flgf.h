@@ -97,10 +97,12 @@ void flgf_destroy(flgf_ctx* ctx);
  *                      work of the dense parent-group kernel (8 x 8 children of
  *                      every neighbour parent pair, absent blocks included)
  *                      runs on the pair-list kernel instead; 0 = never.
- *   FLGF_CTX_TILE      dense tile in parents, t0 | t1 << 8 | t2 << 16 with
+ *   FLGF_CTX_TILE      tile in parents, t0 | t1 << 8 | t2 << 16 with
  *                      1 <= t_a <= 8, t0 t1 t2 <= 128 and
- *                      (t0 + 2)(t1 + 2)(t2 + 2) <= 397 (the tile's source
- *                      region must fit shared memory); default 4 x 4 x 8.
+ *                      (t0 + 2)(t1 + 2)(t2 + 2) <= 397; default 4 x 4 x 8.
+ *                      Tiles are the unit of the pair-list decision, and
+ *                      their order is the order in which parents are packed
+ *                      into the dense kernel's groups.
  * FLGF_EINVAL for an unknown key or a value out of range. */
 enum { FLGF_CTX_LIST_PCT = 1, FLGF_CTX_TILE = 2 };
 int flgf_ctx_set_option(flgf_ctx* ctx, int key, int value);

@@ -101,9 +101,10 @@ template <typename R>
 cudaError_t launch_hadamard(int N, const HadGroup* groups, const HadWork* work, int nwork, int max_units,
                             const int* src_ids, const int* tgt_ids, const int16_t* par_tab, const void* spec, void* acc,
                             int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s);
-// Sparse tiles: explicit (target, source) pair lists.  A group holds up to
-// kListTargets existing targets of one tile (sorted by list length), the
-// union of their existing sources, and per target its pair entries
+// Sparse tiles: explicit (target, source) pair lists.  The targets of the
+// sparse tiles of one octree level are pooled in tile order and cut into
+// groups of up to kListTargets targets (sorted by list length within a group)
+// whose source union fits shared memory; per target the pair entries are
 // (local source slot << 9 | kernel offset index), stored entry-major
 // [entry][kListTargets] so a warp reads consecutive words.
 constexpr int kListTargets = 128;
