@@ -174,7 +174,9 @@ int flgf_laplacian(flgf_blockset* bs, int problem, int level, const void* u, voi
  * and target sets swapped.  The gradient of a loss with dL/du = g is then
  * dL/df = A^T g, zero on non-leaf blocks.  Seeds persist until reloaded; the
  * potentials of the last flgf_solve stay valid.
- * Enqueued on the context stream; the source correction option applies. */
+ * Enqueued on the context stream; the source correction option applies.  The
+ * first flgf_load_adjoint or flgf_solve_adjoint of a block set builds its
+ * adjoint lists and allocates the adjoint buffers (FLGF_ENOMEM on failure). */
 int flgf_load_adjoint(flgf_blockset* bs, int problem, int level, const void* g, int where);
 int flgf_solve_adjoint(flgf_blockset* bs);
 int flgf_get_gradient(flgf_blockset* bs, int problem, int level, void* out, int where);

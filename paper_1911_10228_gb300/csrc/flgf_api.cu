@@ -189,6 +189,9 @@ struct flgf_blockset {
   // solve in flight has copied the source buffer (ev_fuser_free), so they
   // overlap the rest of that solve; the next solve waits for ev_loaded
   cudaStream_t cstream = nullptr;
+  // adjoint lists and buffers, built on first use (flgf_load_adjoint / flgf_solve_adjoint)
+  Arena aar;
+  bool adj_ready = false;
   cudaEvent_t ev_fuser_free = nullptr, ev_loaded = nullptr, ev_dev_load = nullptr;
   bool load_pending = false;
   bool correction = true, solved = false;
@@ -404,7 +407,310 @@ extern "C" void flgf_blockset_destroy(flgf_blockset* bs) {
   if (bs->ev_loaded) cudaEventDestroy(bs->ev_loaded);
   if (bs->ev_dev_load) cudaEventDestroy(bs->ev_dev_load);
   if (bs->cstream) cudaStreamDestroy(bs->cstream);
+  cudaFree(bs->aar.dev);
   delete bs;
+}
+
+// FMM launch lists of phase l for the given instances (their is_src /
+// need_tgt masks select sources and targets), appended to arena ar.
+static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<const Inst*>& insts, PhaseOff& ph, bool count) {
+  flgf_ctx* ctx = bs->ctx;
+  const int N = ctx->N;
+  const int TP[3] = {ctx->tile[0], ctx->tile[1], ctx->tile[2]};  // tile in parents (<= 128: 256 threads)
+  std::vector<int> prep_src, prep_dst;
+  std::vector<uint8_t> prep_zero;
+  int maxtop = 0;
+  for (const Inst* in : insts) maxtop = std::max(maxtop, in->top);
+  std::vector<std::vector<int>> ant_par(maxtop + 1), ant_ch(maxtop + 1);
+  std::vector<std::vector<int>> itp_ch(maxtop + 1), itp_par(maxtop + 1), itp_cpos(maxtop + 1);
+  std::vector<int> fwd_gid, fwd_sid, inv_sid, inv_gid;
+  std::vector<double> inv_scale;
+  // parents with targets of dense tiles per octree level, in tile order
+  std::vector<std::vector<ParentRec>> dpool;
+  std::vector<ListGroup> groups;
+  std::vector<int> l_tgt, l_len, l_ent, l_src;
+  int max_group_src = 0;
+  // targets of sparse tiles per octree level, in tile order: (target id, pair list)
+  std::vector<std::vector<std::pair<int, std::vector<int>>>> lpool;
+  const int nchunk = ctx->prec == FLGF_FP64 ? nchunks<double>(N) : nchunks<float>(N);
+  for (const Inst* inp : insts) {
+    const Inst& in = *inp;
+    const LevelInfo& L = bs->prob[in.p].lev[l];
+    for (size_t b = 0; b < L.c.size(); ++b) {
+      prep_src.push_back(L.fw0 + (int)b);
+      prep_dst.push_back(in.gid0[0] + (int)b);
+      prep_zero.push_back(in.variant == 1 && !L.leaf[b]);
+    }
+    for (int k = 1; k <= in.top; ++k) {
+      for (size_t i = 0; i < in.lv[k].size(); ++i) {
+        const I3& c = in.lv[k][i];
+        ant_par[k].push_back(in.gid0[k] + (int)i);
+        for (int a = 0; a < 8; ++a) {
+          const I3 ch = {2 * c[0] + (a >> 2), 2 * c[1] + ((a >> 1) & 1), 2 * c[2] + (a & 1)};
+          auto it = in.idx[k - 1].find(key3(ch));
+          ant_ch[k].push_back(it == in.idx[k - 1].end() ? -1 : in.gid0[k - 1] + it->second);
+        }
+      }
+    }
+    for (size_t k = 0; k < in.lv.size(); ++k) {
+      for (size_t i = 0; i < in.lv[k].size(); ++i) {
+        const int gid = in.gid0[k] + (int)i;
+        if (in.is_src[k][i]) {
+          fwd_gid.push_back(gid);
+          fwd_sid.push_back(gid - ph.gid_begin);
+        }
+        if (in.need_tgt[k][i]) {
+          inv_sid.push_back(gid - ph.gid_begin);
+          inv_gid.push_back(gid);
+          inv_scale.push_back(in.h * in.h);
+          if ((int)k < in.top) {
+            const I3& c = in.lv[k][i];
+            const int pi = in.idx[k + 1].at(key3(c[0] >> 1, c[1] >> 1, c[2] >> 1));
+            itp_ch[k].push_back(gid);
+            itp_par[k].push_back(in.gid0[k + 1] + pi);
+            itp_cpos[k].push_back(((c[0] & 1) << 2) | ((c[1] & 1) << 1) | (c[2] & 1));
+          }
+        }
+      }
+      // interaction tiles of this octree level
+      I3 lo = {INT32_MAX, INT32_MAX, INT32_MAX}, hi = {INT32_MIN, INT32_MIN, INT32_MIN};
+      for (const auto& c : in.lv[k])
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = std::min(lo[a], c[a] >> 1);
+          hi[a] = std::max(hi[a], c[a] >> 1);
+        }
+      // block index by coordinates: a dense grid over the level's box when it is
+      // small enough (every lookup below stays inside [2 lo, 2 hi + 1]), else the hash map
+      const I3 glo = {2 * lo[0], 2 * lo[1], 2 * lo[2]};
+      const int64_t gd[3] = {2 * (int64_t)(hi[0] - lo[0]) + 2, 2 * (int64_t)(hi[1] - lo[1]) + 2,
+                             2 * (int64_t)(hi[2] - lo[2]) + 2};
+      const bool dense = gd[0] * gd[1] * gd[2] <= ((int64_t)1 << 24);
+      std::vector<int> grid;
+      if (dense) {
+        grid.assign((size_t)(gd[0] * gd[1] * gd[2]), -1);
+        for (size_t i = 0; i < in.lv[k].size(); ++i) {
+          const I3& c = in.lv[k][i];
+          grid[((size_t)(c[0] - glo[0]) * gd[1] + (c[1] - glo[1])) * gd[2] + (c[2] - glo[2])] = (int)i;
+        }
+      }
+      auto lookup = [&](int a, int b, int c2) -> int {
+        if (dense) {
+          const int64_t x = a - glo[0], y = b - glo[1], z = c2 - glo[2];
+          if (x < 0 || y < 0 || z < 0 || x >= gd[0] || y >= gd[1] || z >= gd[2]) return -1;
+          return grid[((size_t)x * gd[1] + y) * gd[2] + z];
+        }
+        auto it = in.idx[k].find(key3(a, b, c2));
+        return it == in.idx[k].end() ? -1 : it->second;
+      };
+      const bool excl = k > 0;
+      for (int t0 = lo[0]; t0 <= hi[0]; t0 += TP[0])
+        for (int t1 = lo[1]; t1 <= hi[1]; t1 += TP[1])
+          for (int t2 = lo[2]; t2 <= hi[2]; t2 += TP[2]) {
+            struct { int P[3], r0[3], Rg[3]; } tl;  // tile and its region (tile + 1 parent, clipped)
+            const int t[3] = {t0, t1, t2};
+            for (int a = 0; a < 3; ++a) {
+              tl.P[a] = std::min(TP[a], hi[a] - t[a] + 1);
+              tl.r0[a] = std::max(t[a] - 1, lo[a]);
+              tl.Rg[a] = std::min(t[a] + tl.P[a], hi[a]) - tl.r0[a] + 1;
+            }
+            std::vector<int> tg;
+            bool any = false;
+            for (int x = 0; x < 2 * tl.P[0]; ++x)
+              for (int y = 0; y < 2 * tl.P[1]; ++y)
+                for (int z = 0; z < 2 * tl.P[2]; ++z) {
+                  const int i = lookup(2 * t0 + x, 2 * t1 + y, 2 * t2 + z);
+                  const bool need = i >= 0 && in.need_tgt[k][i];
+                  tg.push_back(need ? in.gid0[k] + i - ph.gid_begin : -1);
+                  any |= need;
+                }
+            if (!any) continue;
+            // source slots in parity-major order: slot = b * NQ + q
+            const int NQ = tl.Rg[0] * tl.Rg[1] * tl.Rg[2];
+            std::vector<int> sg(8 * NQ, -1);
+            for (int x = 0; x < 2 * tl.Rg[0]; ++x)
+              for (int y = 0; y < 2 * tl.Rg[1]; ++y)
+                for (int z = 0; z < 2 * tl.Rg[2]; ++z) {
+                  const int i = lookup(2 * tl.r0[0] + x, 2 * tl.r0[1] + y, 2 * tl.r0[2] + z);
+                  const int b = ((x & 1) << 2) | ((y & 1) << 1) | (z & 1);
+                  const int qq = ((x >> 1) * tl.Rg[1] + (y >> 1)) * tl.Rg[2] + (z >> 1);
+                  sg[b * NQ + qq] = i >= 0 && in.is_src[k][i] ? in.gid0[k] + i - ph.gid_begin : -1;
+                }
+            // the interacting (target, source) pairs of every target: the
+            // candidates are the children of its parent's 27 neighbours
+            std::vector<std::vector<int>> plist(tg.size());  // (source id << 9) | offset index
+            int64_t useful = 0;
+            for (int x = 0; x < 2 * tl.P[0]; ++x)
+              for (int y = 0; y < 2 * tl.P[1]; ++y)
+                for (int z = 0; z < 2 * tl.P[2]; ++z) {
+                  const int ti = (x * 2 * tl.P[1] + y) * 2 * tl.P[2] + z;
+                  if (tg[ti] < 0) continue;
+                  const int tc[3] = {2 * t0 + x, 2 * t1 + y, 2 * t2 + z};
+                  for (int e = 0; e < 27; ++e)
+                    for (int b = 0; b < 8; ++b) {
+                      const int sc[3] = {2 * ((tc[0] >> 1) + e / 9 - 1) + (b >> 2),
+                                         2 * ((tc[1] >> 1) + (e / 3) % 3 - 1) + ((b >> 1) & 1),
+                                         2 * ((tc[2] >> 1) + e % 3 - 1) + (b & 1)};
+                      int rr[3];
+                      bool in = true, near = true;
+                      for (int a = 0; a < 3; ++a) {
+                        rr[a] = sc[a] - 2 * tl.r0[a];
+                        in &= rr[a] >= 0 && rr[a] < 2 * tl.Rg[a];
+                        near &= std::abs(sc[a] - tc[a]) <= 1;
+                      }
+                      if (!in || (excl && near)) continue;
+                      const int bb = ((rr[0] & 1) << 2) | ((rr[1] & 1) << 1) | (rr[2] & 1);
+                      const int qq = ((rr[0] >> 1) * tl.Rg[1] + (rr[1] >> 1)) * tl.Rg[2] + (rr[2] >> 1);
+                      const int sid = sg[bb * NQ + qq];
+                      if (sid < 0) continue;
+                      plist[ti].push_back((sid << 9) | off_index(tc[0] - sc[0], tc[1] - sc[1], tc[2] - sc[2]));
+                    }
+                  useful += (int64_t)plist[ti].size();
+                }
+            if (count) bs->pairs += useful;
+            // parent records of the tile's parents that have targets
+            std::vector<ParentRec> recs;
+            int64_t dense = 0;  // complex MACs per frequency of the parent-group kernel
+            for (int p0 = 0; p0 < tl.P[0]; ++p0)
+              for (int p1 = 0; p1 < tl.P[1]; ++p1)
+                for (int p2 = 0; p2 < tl.P[2]; ++p2) {
+                  ParentRec r;
+                  bool has = false;
+                  for (int a = 0; a < 8; ++a) {
+                    r.tgt[a] = tg[((2 * p0 + (a >> 2)) * 2 * tl.P[1] + 2 * p1 + ((a >> 1) & 1)) * 2 * tl.P[2] + 2 * p2 +
+                                  (a & 1)];
+                    has |= r.tgt[a] >= 0;
+                  }
+                  if (!has) continue;
+                  const int pc[3] = {t0 + p0, t1 + p1, t2 + p2};
+                  for (int e = 0; e < 27; ++e) {
+                    const int ee[3] = {e / 9 - 1, (e / 3) % 3 - 1, e % 3 - 1};
+                    int q[3];
+                    bool inr = !(excl && e == 13);
+                    for (int a = 0; a < 3; ++a) {
+                      q[a] = pc[a] + ee[a] - tl.r0[a];
+                      inr &= q[a] >= 0 && q[a] < tl.Rg[a];
+                    }
+                    bool any_src = false;
+                    for (int b = 0; b < 8; ++b) {
+                      r.cell[e][b] = inr ? sg[b * NQ + (q[0] * tl.Rg[1] + q[1]) * tl.Rg[2] + q[2]] : -1;
+                      any_src |= r.cell[e][b] >= 0;
+                    }
+                    dense += any_src ? 64 : 0;
+                  }
+                  recs.push_back(r);
+                }
+            if (useful * 100 < (int64_t)ctx->list_pct * dense) {
+              // sparse tile: its targets join the pair-list pool of octree level k
+              if ((int)lpool.size() <= (int)k) lpool.resize(k + 1);
+              for (int ti = 0; ti < (int)tg.size(); ++ti)
+                if (tg[ti] >= 0) lpool[k].push_back({tg[ti], std::move(plist[ti])});
+              continue;
+            }
+            if ((int)dpool.size() <= (int)k) dpool.resize(k + 1);
+            dpool[k].insert(dpool[k].end(), recs.begin(), recs.end());
+          }
+    }
+  }
+  // dense MAC: parent groups of every octree level
+  HadLists hl;
+  for (int k = 0; k < (int)dpool.size(); ++k)
+    pack_parent_groups(k, dpool[k], nchunk, had_kernel_units(ctx->prec == FLGF_FP64), hl);
+  // pair-list groups: consecutive pool targets (spatially close, so their
+  // source sets overlap) up to kListTargets targets or kListMaxSrc sources
+  for (int k = 0; k < (int)lpool.size(); ++k) {
+    const auto& pool = lpool[k];
+    size_t pos = 0;
+    while (pos < pool.size()) {
+      std::unordered_map<int, int> slot;
+      std::vector<int> gsrc, members;
+      while (pos < pool.size() && (int)members.size() < kListTargets) {
+        const auto& pl = pool[pos].second;
+        int add = 0;
+        for (int w : pl) add += slot.count(w >> 9) ? 0 : 1;
+        if (!members.empty() && (int)gsrc.size() + add > kListMaxSrc) break;
+        for (int w : pl)
+          if (!slot.count(w >> 9)) {
+            slot.emplace(w >> 9, (int)gsrc.size());
+            gsrc.push_back(w >> 9);
+          }
+        members.push_back((int)pos++);
+      }
+      // longest lists first: the threads of a warp run similar trip counts
+      std::stable_sort(members.begin(), members.end(),
+                       [&](int a, int b) { return pool[a].second.size() > pool[b].second.size(); });
+      ListGroup g;
+      g.level = k;
+      g.ntgt = (int)members.size();
+      g.maxlen = (int)pool[members[0]].second.size();
+      g.tgt_off = (int)l_tgt.size();
+      g.len_off = (int)l_len.size();
+      g.ent_off = (int)l_ent.size();
+      g.src_off = (int)l_src.size();
+      g.nsrc = (int)gsrc.size();
+      l_ent.resize(l_ent.size() + (size_t)g.maxlen * kListTargets, 0);
+      for (int m = 0; m < g.ntgt; ++m) {
+        const auto& pl = pool[members[m]].second;
+        l_tgt.push_back(pool[members[m]].first);
+        l_len.push_back((int)pl.size());
+        for (size_t j = 0; j < pl.size(); ++j)
+          l_ent[g.ent_off + j * kListTargets + m] = (slot.at(pl[j] >> 9) << 9) | (pl[j] & 511);
+      }
+      l_src.insert(l_src.end(), gsrc.begin(), gsrc.end());
+      max_group_src = std::max(max_group_src, g.nsrc);
+      groups.push_back(g);
+    }
+  }
+  if (count) {
+    bs->n_fwd += (int64_t)fwd_gid.size();
+    bs->n_inv += (int64_t)inv_gid.size();
+    for (int k = 0; k <= maxtop; ++k) bs->n_koff += kNOff;
+  }
+  ph.n_prep = (int)prep_src.size();
+  ph.prep_src = ar.add(prep_src);
+  ph.prep_dst = ar.add(prep_dst);
+  ph.prep_zero = ar.add(prep_zero);
+  ph.n_ant.assign(maxtop + 1, 0);
+  ph.ant_par.assign(maxtop + 1, 0);
+  ph.ant_ch.assign(maxtop + 1, 0);
+  ph.n_itp.assign(maxtop + 1, 0);
+  ph.itp_ch.assign(maxtop + 1, 0);
+  ph.itp_par.assign(maxtop + 1, 0);
+  ph.itp_cpos.assign(maxtop + 1, 0);
+  for (int k = 0; k <= maxtop; ++k) {
+    ph.n_ant[k] = (int)ant_par[k].size();
+    ph.ant_par[k] = ar.add(ant_par[k]);
+    ph.ant_ch[k] = ar.add(ant_ch[k]);
+    ph.n_itp[k] = (int)itp_ch[k].size();
+    ph.itp_ch[k] = ar.add(itp_ch[k]);
+    ph.itp_par[k] = ar.add(itp_par[k]);
+    ph.itp_cpos[k] = ar.add(itp_cpos[k]);
+  }
+  ph.n_fwd = (int)fwd_gid.size();
+  ph.fwd_gid = ar.add(fwd_gid);
+  ph.fwd_sid = ar.add(fwd_sid);
+  ph.n_groups_dense = (int)hl.groups.size();
+  ph.hgroups = ar.add(hl.groups);
+  ph.max_units = hl.max_units;
+  std::vector<HadWork>& work = hl.work;
+  // chunk-major order: the groups sharing a frequency chunk run back to back,
+  // so the chunk's kernel spectra and the shared halo spectra stay in L2
+  std::stable_sort(work.begin(), work.end(), [](const HadWork& x, const HadWork& y) { return x.chunk0 < y.chunk0; });
+  ph.n_work = (int)work.size();
+  ph.work = ar.add(work);
+  ph.src_ids = ar.add(hl.src_ids);
+  ph.tgt_ids = ar.add(hl.tgt_ids);
+  ph.par_tab = ar.add(hl.par_tab);
+  ph.n_groups = (int)groups.size();
+  ph.max_group_src = max_group_src;
+  ph.groups = ar.add(groups);
+  ph.l_tgt = ar.add(l_tgt);
+  ph.l_len = ar.add(l_len);
+  ph.l_ent = ar.add(l_ent);
+  ph.l_src = ar.add(l_src);
+  ph.n_inv = (int)inv_gid.size();
+  ph.inv_sid = ar.add(inv_sid);
+  ph.inv_gid = ar.add(inv_gid);
+  ph.inv_scale = ar.add(inv_scale);
 }
 
 extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
@@ -552,292 +858,12 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     return bail(FLGF_EINVAL, "more than 2^22 octree blocks in one refinement level");
   // ---- launch lists ----------------------------------------------------------
   Arena& ar = bs->ar;
-  const int TP[3] = {ctx->tile[0], ctx->tile[1], ctx->tile[2]};  // tile in parents (<= 128: 256 threads)
-  // FMM launch lists of phase l for the given instances (their is_src /
-  // need_tgt masks select sources and targets)
-  auto build_fmm = [&](int l, const std::vector<const Inst*>& insts, PhaseOff& ph, bool count) {
-    std::vector<int> prep_src, prep_dst;
-    std::vector<uint8_t> prep_zero;
-    int maxtop = 0;
-    for (const Inst* in : insts) maxtop = std::max(maxtop, in->top);
-    std::vector<std::vector<int>> ant_par(maxtop + 1), ant_ch(maxtop + 1);
-    std::vector<std::vector<int>> itp_ch(maxtop + 1), itp_par(maxtop + 1), itp_cpos(maxtop + 1);
-    std::vector<int> fwd_gid, fwd_sid, inv_sid, inv_gid;
-    std::vector<double> inv_scale;
-    // parents with targets of dense tiles per octree level, in tile order
-    std::vector<std::vector<ParentRec>> dpool;
-    std::vector<ListGroup> groups;
-    std::vector<int> l_tgt, l_len, l_ent, l_src;
-    int max_group_src = 0;
-    // targets of sparse tiles per octree level, in tile order: (target id, pair list)
-    std::vector<std::vector<std::pair<int, std::vector<int>>>> lpool;
-    const int nchunk = ctx->prec == FLGF_FP64 ? nchunks<double>(N) : nchunks<float>(N);
-    for (const Inst* inp : insts) {
-      const Inst& in = *inp;
-      const LevelInfo& L = bs->prob[in.p].lev[l];
-      for (size_t b = 0; b < L.c.size(); ++b) {
-        prep_src.push_back(L.fw0 + (int)b);
-        prep_dst.push_back(in.gid0[0] + (int)b);
-        prep_zero.push_back(in.variant == 1 && !L.leaf[b]);
-      }
-      for (int k = 1; k <= in.top; ++k) {
-        for (size_t i = 0; i < in.lv[k].size(); ++i) {
-          const I3& c = in.lv[k][i];
-          ant_par[k].push_back(in.gid0[k] + (int)i);
-          for (int a = 0; a < 8; ++a) {
-            const I3 ch = {2 * c[0] + (a >> 2), 2 * c[1] + ((a >> 1) & 1), 2 * c[2] + (a & 1)};
-            auto it = in.idx[k - 1].find(key3(ch));
-            ant_ch[k].push_back(it == in.idx[k - 1].end() ? -1 : in.gid0[k - 1] + it->second);
-          }
-        }
-      }
-      for (size_t k = 0; k < in.lv.size(); ++k) {
-        for (size_t i = 0; i < in.lv[k].size(); ++i) {
-          const int gid = in.gid0[k] + (int)i;
-          if (in.is_src[k][i]) {
-            fwd_gid.push_back(gid);
-            fwd_sid.push_back(gid - ph.gid_begin);
-          }
-          if (in.need_tgt[k][i]) {
-            inv_sid.push_back(gid - ph.gid_begin);
-            inv_gid.push_back(gid);
-            inv_scale.push_back(in.h * in.h);
-            if ((int)k < in.top) {
-              const I3& c = in.lv[k][i];
-              const int pi = in.idx[k + 1].at(key3(c[0] >> 1, c[1] >> 1, c[2] >> 1));
-              itp_ch[k].push_back(gid);
-              itp_par[k].push_back(in.gid0[k + 1] + pi);
-              itp_cpos[k].push_back(((c[0] & 1) << 2) | ((c[1] & 1) << 1) | (c[2] & 1));
-            }
-          }
-        }
-        // interaction tiles of this octree level
-        I3 lo = {INT32_MAX, INT32_MAX, INT32_MAX}, hi = {INT32_MIN, INT32_MIN, INT32_MIN};
-        for (const auto& c : in.lv[k])
-          for (int a = 0; a < 3; ++a) {
-            lo[a] = std::min(lo[a], c[a] >> 1);
-            hi[a] = std::max(hi[a], c[a] >> 1);
-          }
-        auto lookup = [&](int a, int b, int c2) -> int {
-          auto it = in.idx[k].find(key3(a, b, c2));
-          return it == in.idx[k].end() ? -1 : it->second;
-        };
-        const bool excl = k > 0;
-        for (int t0 = lo[0]; t0 <= hi[0]; t0 += TP[0])
-          for (int t1 = lo[1]; t1 <= hi[1]; t1 += TP[1])
-            for (int t2 = lo[2]; t2 <= hi[2]; t2 += TP[2]) {
-              struct { int P[3], r0[3], Rg[3]; } tl;  // tile and its region (tile + 1 parent, clipped)
-              const int t[3] = {t0, t1, t2};
-              for (int a = 0; a < 3; ++a) {
-                tl.P[a] = std::min(TP[a], hi[a] - t[a] + 1);
-                tl.r0[a] = std::max(t[a] - 1, lo[a]);
-                tl.Rg[a] = std::min(t[a] + tl.P[a], hi[a]) - tl.r0[a] + 1;
-              }
-              std::vector<int> tg;
-              bool any = false;
-              for (int x = 0; x < 2 * tl.P[0]; ++x)
-                for (int y = 0; y < 2 * tl.P[1]; ++y)
-                  for (int z = 0; z < 2 * tl.P[2]; ++z) {
-                    const int i = lookup(2 * t0 + x, 2 * t1 + y, 2 * t2 + z);
-                    const bool need = i >= 0 && in.need_tgt[k][i];
-                    tg.push_back(need ? in.gid0[k] + i - ph.gid_begin : -1);
-                    any |= need;
-                  }
-              if (!any) continue;
-              // source slots in parity-major order: slot = b * NQ + q
-              const int NQ = tl.Rg[0] * tl.Rg[1] * tl.Rg[2];
-              std::vector<int> sg(8 * NQ, -1);
-              for (int x = 0; x < 2 * tl.Rg[0]; ++x)
-                for (int y = 0; y < 2 * tl.Rg[1]; ++y)
-                  for (int z = 0; z < 2 * tl.Rg[2]; ++z) {
-                    const int i = lookup(2 * tl.r0[0] + x, 2 * tl.r0[1] + y, 2 * tl.r0[2] + z);
-                    const int b = ((x & 1) << 2) | ((y & 1) << 1) | (z & 1);
-                    const int qq = ((x >> 1) * tl.Rg[1] + (y >> 1)) * tl.Rg[2] + (z >> 1);
-                    sg[b * NQ + qq] = i >= 0 && in.is_src[k][i] ? in.gid0[k] + i - ph.gid_begin : -1;
-                  }
-              // the interacting (target, source) pairs of every target: the
-              // candidates are the children of its parent's 27 neighbours
-              std::vector<std::vector<int>> plist(tg.size());  // (source id << 9) | offset index
-              int64_t useful = 0;
-              for (int x = 0; x < 2 * tl.P[0]; ++x)
-                for (int y = 0; y < 2 * tl.P[1]; ++y)
-                  for (int z = 0; z < 2 * tl.P[2]; ++z) {
-                    const int ti = (x * 2 * tl.P[1] + y) * 2 * tl.P[2] + z;
-                    if (tg[ti] < 0) continue;
-                    const int tc[3] = {2 * t0 + x, 2 * t1 + y, 2 * t2 + z};
-                    for (int e = 0; e < 27; ++e)
-                      for (int b = 0; b < 8; ++b) {
-                        const int sc[3] = {2 * ((tc[0] >> 1) + e / 9 - 1) + (b >> 2),
-                                           2 * ((tc[1] >> 1) + (e / 3) % 3 - 1) + ((b >> 1) & 1),
-                                           2 * ((tc[2] >> 1) + e % 3 - 1) + (b & 1)};
-                        int rr[3];
-                        bool in = true, near = true;
-                        for (int a = 0; a < 3; ++a) {
-                          rr[a] = sc[a] - 2 * tl.r0[a];
-                          in &= rr[a] >= 0 && rr[a] < 2 * tl.Rg[a];
-                          near &= std::abs(sc[a] - tc[a]) <= 1;
-                        }
-                        if (!in || (excl && near)) continue;
-                        const int bb = ((rr[0] & 1) << 2) | ((rr[1] & 1) << 1) | (rr[2] & 1);
-                        const int qq = ((rr[0] >> 1) * tl.Rg[1] + (rr[1] >> 1)) * tl.Rg[2] + (rr[2] >> 1);
-                        const int sid = sg[bb * NQ + qq];
-                        if (sid < 0) continue;
-                        plist[ti].push_back((sid << 9) | off_index(tc[0] - sc[0], tc[1] - sc[1], tc[2] - sc[2]));
-                      }
-                    useful += (int64_t)plist[ti].size();
-                  }
-              if (count) bs->pairs += useful;
-              // parent records of the tile's parents that have targets
-              std::vector<ParentRec> recs;
-              int64_t dense = 0;  // complex MACs per frequency of the parent-group kernel
-              for (int p0 = 0; p0 < tl.P[0]; ++p0)
-                for (int p1 = 0; p1 < tl.P[1]; ++p1)
-                  for (int p2 = 0; p2 < tl.P[2]; ++p2) {
-                    ParentRec r;
-                    bool has = false;
-                    for (int a = 0; a < 8; ++a) {
-                      r.tgt[a] = tg[((2 * p0 + (a >> 2)) * 2 * tl.P[1] + 2 * p1 + ((a >> 1) & 1)) * 2 * tl.P[2] + 2 * p2 +
-                                    (a & 1)];
-                      has |= r.tgt[a] >= 0;
-                    }
-                    if (!has) continue;
-                    const int pc[3] = {t0 + p0, t1 + p1, t2 + p2};
-                    for (int e = 0; e < 27; ++e) {
-                      const int ee[3] = {e / 9 - 1, (e / 3) % 3 - 1, e % 3 - 1};
-                      int q[3];
-                      bool inr = !(excl && e == 13);
-                      for (int a = 0; a < 3; ++a) {
-                        q[a] = pc[a] + ee[a] - tl.r0[a];
-                        inr &= q[a] >= 0 && q[a] < tl.Rg[a];
-                      }
-                      bool any_src = false;
-                      for (int b = 0; b < 8; ++b) {
-                        r.cell[e][b] = inr ? sg[b * NQ + (q[0] * tl.Rg[1] + q[1]) * tl.Rg[2] + q[2]] : -1;
-                        any_src |= r.cell[e][b] >= 0;
-                      }
-                      dense += any_src ? 64 : 0;
-                    }
-                    recs.push_back(r);
-                  }
-              if (useful * 100 < (int64_t)ctx->list_pct * dense) {
-                // sparse tile: its targets join the pair-list pool of octree level k
-                if ((int)lpool.size() <= (int)k) lpool.resize(k + 1);
-                for (int ti = 0; ti < (int)tg.size(); ++ti)
-                  if (tg[ti] >= 0) lpool[k].push_back({tg[ti], std::move(plist[ti])});
-                continue;
-              }
-              if ((int)dpool.size() <= (int)k) dpool.resize(k + 1);
-              dpool[k].insert(dpool[k].end(), recs.begin(), recs.end());
-            }
-      }
-    }
-    // dense MAC: parent groups of every octree level
-    HadLists hl;
-    for (int k = 0; k < (int)dpool.size(); ++k)
-      pack_parent_groups(k, dpool[k], nchunk, had_kernel_units(ctx->prec == FLGF_FP64), hl);
-    // pair-list groups: consecutive pool targets (spatially close, so their
-    // source sets overlap) up to kListTargets targets or kListMaxSrc sources
-    for (int k = 0; k < (int)lpool.size(); ++k) {
-      const auto& pool = lpool[k];
-      size_t pos = 0;
-      while (pos < pool.size()) {
-        std::unordered_map<int, int> slot;
-        std::vector<int> gsrc, members;
-        while (pos < pool.size() && (int)members.size() < kListTargets) {
-          const auto& pl = pool[pos].second;
-          int add = 0;
-          for (int w : pl) add += slot.count(w >> 9) ? 0 : 1;
-          if (!members.empty() && (int)gsrc.size() + add > kListMaxSrc) break;
-          for (int w : pl)
-            if (!slot.count(w >> 9)) {
-              slot.emplace(w >> 9, (int)gsrc.size());
-              gsrc.push_back(w >> 9);
-            }
-          members.push_back((int)pos++);
-        }
-        // longest lists first: the threads of a warp run similar trip counts
-        std::stable_sort(members.begin(), members.end(),
-                         [&](int a, int b) { return pool[a].second.size() > pool[b].second.size(); });
-        ListGroup g;
-        g.level = k;
-        g.ntgt = (int)members.size();
-        g.maxlen = (int)pool[members[0]].second.size();
-        g.tgt_off = (int)l_tgt.size();
-        g.len_off = (int)l_len.size();
-        g.ent_off = (int)l_ent.size();
-        g.src_off = (int)l_src.size();
-        g.nsrc = (int)gsrc.size();
-        l_ent.resize(l_ent.size() + (size_t)g.maxlen * kListTargets, 0);
-        for (int m = 0; m < g.ntgt; ++m) {
-          const auto& pl = pool[members[m]].second;
-          l_tgt.push_back(pool[members[m]].first);
-          l_len.push_back((int)pl.size());
-          for (size_t j = 0; j < pl.size(); ++j)
-            l_ent[g.ent_off + j * kListTargets + m] = (slot.at(pl[j] >> 9) << 9) | (pl[j] & 511);
-        }
-        l_src.insert(l_src.end(), gsrc.begin(), gsrc.end());
-        max_group_src = std::max(max_group_src, g.nsrc);
-        groups.push_back(g);
-      }
-    }
-    if (count) {
-      bs->n_fwd += (int64_t)fwd_gid.size();
-      bs->n_inv += (int64_t)inv_gid.size();
-      for (int k = 0; k <= maxtop; ++k) bs->n_koff += kNOff;
-    }
-    ph.n_prep = (int)prep_src.size();
-    ph.prep_src = ar.add(prep_src);
-    ph.prep_dst = ar.add(prep_dst);
-    ph.prep_zero = ar.add(prep_zero);
-    ph.n_ant.assign(maxtop + 1, 0);
-    ph.ant_par.assign(maxtop + 1, 0);
-    ph.ant_ch.assign(maxtop + 1, 0);
-    ph.n_itp.assign(maxtop + 1, 0);
-    ph.itp_ch.assign(maxtop + 1, 0);
-    ph.itp_par.assign(maxtop + 1, 0);
-    ph.itp_cpos.assign(maxtop + 1, 0);
-    for (int k = 0; k <= maxtop; ++k) {
-      ph.n_ant[k] = (int)ant_par[k].size();
-      ph.ant_par[k] = ar.add(ant_par[k]);
-      ph.ant_ch[k] = ar.add(ant_ch[k]);
-      ph.n_itp[k] = (int)itp_ch[k].size();
-      ph.itp_ch[k] = ar.add(itp_ch[k]);
-      ph.itp_par[k] = ar.add(itp_par[k]);
-      ph.itp_cpos[k] = ar.add(itp_cpos[k]);
-    }
-    ph.n_fwd = (int)fwd_gid.size();
-    ph.fwd_gid = ar.add(fwd_gid);
-    ph.fwd_sid = ar.add(fwd_sid);
-    ph.n_groups_dense = (int)hl.groups.size();
-    ph.hgroups = ar.add(hl.groups);
-    ph.max_units = hl.max_units;
-    std::vector<HadWork>& work = hl.work;
-    // chunk-major order: the groups sharing a frequency chunk run back to back,
-    // so the chunk's kernel spectra and the shared halo spectra stay in L2
-    std::stable_sort(work.begin(), work.end(), [](const HadWork& x, const HadWork& y) { return x.chunk0 < y.chunk0; });
-    ph.n_work = (int)work.size();
-    ph.work = ar.add(work);
-    ph.src_ids = ar.add(hl.src_ids);
-    ph.tgt_ids = ar.add(hl.tgt_ids);
-    ph.par_tab = ar.add(hl.par_tab);
-    ph.n_groups = (int)groups.size();
-    ph.max_group_src = max_group_src;
-    ph.groups = ar.add(groups);
-    ph.l_tgt = ar.add(l_tgt);
-    ph.l_len = ar.add(l_len);
-    ph.l_ent = ar.add(l_ent);
-    ph.l_src = ar.add(l_src);
-    ph.n_inv = (int)inv_gid.size();
-    ph.inv_sid = ar.add(inv_sid);
-    ph.inv_gid = ar.add(inv_gid);
-    ph.inv_scale = ar.add(inv_scale);
-  };
   for (int l = 0; l < bs->Lmax; ++l) {
     PhaseOff& ph = bs->ph[l];
     std::vector<const Inst*> insts;
     for (const auto& in : bs->inst)
       if (in.l == l) insts.push_back(&in);
-    build_fmm(l, insts, ph, true);
+    build_fmm(bs, ar, l, insts, ph, true);
     // multi-resolution coupling lists
     std::vector<int> sel_src, sel_dst, selw_src, selw_dst, acc_nbr, acc_fine, acc_cpos, accw_nbr, accw_fine,
         accw_cpos, cor_nbr, cor_fine, cor_cpos, crs_c, crs_f;
@@ -923,7 +949,60 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     ph.crs_coarse = ar.add(crs_c);
     ph.crs_fine = ar.add(crs_f);
   }
-  // ---- adjoint: transposed leaf-only instances and lists --------------------
+  // face neighbours for the Laplacian
+  for (auto& P : bs->prob)
+    for (auto& L : P.lev) {
+      std::vector<int> n6;
+      for (const auto& c : L.c)
+        for (int a = 0; a < 3; ++a)
+          for (int sg = 0; sg < 2; ++sg) {
+            I3 y = c;
+            y[a] += sg == 0 ? 1 : -1;
+            auto it = L.idx.find(key3(y));
+            n6.push_back(it == L.idx.end() ? -1 : it->second);
+          }
+      L.nbr6_off = ar.add(n6);
+    }
+  // ---- device memory ---------------------------------------------------------
+  const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4;
+  const size_t NW = (size_t)nfreq(N);
+  auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 256)); };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = alloc((void**)&ar.dev, ar.host.size());
+  if (e == cudaSuccess) e = cudaMemcpy(ar.dev, ar.host.data(), ar.host.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = alloc(&bs->nodes, rs * N3 * bs->G);
+  if (e == cudaSuccess) e = alloc(&bs->unodes, rs * N3 * bs->G);
+  if (e == cudaSuccess) e = alloc(&bs->fuser, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = alloc(&bs->fwork, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = alloc(&bs->wfield, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = alloc(&bs->spec, 2 * rs * NW * bs->max_phase_blocks);
+  if (e == cudaSuccess) e = alloc(&bs->acc, 2 * rs * NW * bs->max_phase_blocks);
+  if (e == cudaSuccess) e = alloc(&bs->lap_in, rs * N3 * bs->max_level_blocks);
+  if (e == cudaSuccess) e = alloc(&bs->lap_out, rs * N3 * bs->max_level_blocks);
+  if (e == cudaSuccess) e = alloc((void**)&bs->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(bs->fuser, 0, rs * N3 * bs->B);
+  if (e == cudaSuccess) e = cudaMemset(bs->unodes, 0, rs * N3 * bs->G);
+  if (e == cudaSuccess) e = cudaMemset(bs->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs->cstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->ev_fuser_free, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->ev_loaded, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->ev_dev_load, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? FLGF_ENOMEM : FLGF_ECUDA;
+    return bail(code, std::string("blockset allocation: ") + cudaGetErrorString(e));
+  }
+  *out = bs;
+  return FLGF_OK;
+}
+
+// Adjoint plan, built on first use: the transposed leaf-only instances, their
+// FMM lists and the transposed coupling lists (in their own arena), and the
+// adjoint buffers.  Forward-only users pay neither its host time nor its
+// device memory.
+static int build_adjoint(flgf_blockset* bs) {
+  flgf_ctx* ctx = bs->ctx;
+  const size_t N3 = (size_t)ctx->N * ctx->N * ctx->N;
+  Arena& aar = bs->aar;
   bs->aph.resize(bs->Lmax);
   bs->adj.resize(bs->Lmax);
   bs->adj_inst.reserve(bs->inst.size());
@@ -953,11 +1032,11 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
       if (in.l == l) insts.push_back(&in);
     bs->aph[l].gid_begin = bs->ph[l].gid_begin;
     bs->aph[l].nblocks = bs->ph[l].nblocks;
-    build_fmm(l, insts, bs->aph[l], false);
+    build_fmm(bs, aar, l, insts, bs->aph[l], false);
     AdjOff& ao = bs->adj[l];
     std::vector<int> pd, p1, p2, gd, g1, g2, td, t1, t2, c0n, c0f, c0c, c1n, c1f, c1c;
     std::vector<double> c1h;
-    for (int p = 0; p < n_problems; ++p) {
+    for (int p = 0; p < (int)bs->prob.size(); ++p) {
       Problem& P = bs->prob[p];
       if (l >= P.L) continue;
       LevelInfo& L = P.lev[l];
@@ -1009,62 +1088,28 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
         }
       }
     }
-    ao.n_prep = (int)pd.size(); ao.prep_dst = ar.add(pd); ao.prep_s1 = ar.add(p1); ao.prep_s2 = ar.add(p2);
-    ao.n_gacc = (int)gd.size(); ao.gacc_dst = ar.add(gd); ao.gacc_s1 = ar.add(g1); ao.gacc_s2 = ar.add(g2);
-    ao.n_gtmp = (int)td.size(); ao.gtmp_dst = ar.add(td); ao.gtmp_s1 = ar.add(t1); ao.gtmp_s2 = ar.add(t2);
-    ao.n_cf0 = (int)c0f.size(); ao.cf0_nbr = ar.add(c0n); ao.cf0_fine = ar.add(c0f); ao.cf0_cpos = ar.add(c0c);
-    ao.n_cf1 = (int)c1f.size(); ao.cf1_nbr = ar.add(c1n); ao.cf1_fine = ar.add(c1f); ao.cf1_cpos = ar.add(c1c);
-    ao.cf1_ih2 = ar.add(c1h);
+    ao.n_prep = (int)pd.size(); ao.prep_dst = aar.add(pd); ao.prep_s1 = aar.add(p1); ao.prep_s2 = aar.add(p2);
+    ao.n_gacc = (int)gd.size(); ao.gacc_dst = aar.add(gd); ao.gacc_s1 = aar.add(g1); ao.gacc_s2 = aar.add(g2);
+    ao.n_gtmp = (int)td.size(); ao.gtmp_dst = aar.add(td); ao.gtmp_s1 = aar.add(t1); ao.gtmp_s2 = aar.add(t2);
+    ao.n_cf0 = (int)c0f.size(); ao.cf0_nbr = aar.add(c0n); ao.cf0_fine = aar.add(c0f); ao.cf0_cpos = aar.add(c0c);
+    ao.n_cf1 = (int)c1f.size(); ao.cf1_nbr = aar.add(c1n); ao.cf1_fine = aar.add(c1f); ao.cf1_cpos = aar.add(c1c);
+    ao.cf1_ih2 = aar.add(c1h);
   }
-  // face neighbours for the Laplacian
-  for (auto& P : bs->prob)
-    for (auto& L : P.lev) {
-      std::vector<int> n6;
-      for (const auto& c : L.c)
-        for (int a = 0; a < 3; ++a)
-          for (int sg = 0; sg < 2; ++sg) {
-            I3 y = c;
-            y[a] += sg == 0 ? 1 : -1;
-            auto it = L.idx.find(key3(y));
-            n6.push_back(it == L.idx.end() ? -1 : it->second);
-          }
-      L.nbr6_off = ar.add(n6);
-    }
-  // ---- device memory ---------------------------------------------------------
   const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4;
-  const size_t NW = (size_t)nfreq(N);
   auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 256)); };
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = alloc((void**)&ar.dev, ar.host.size());
-  if (e == cudaSuccess) e = cudaMemcpy(ar.dev, ar.host.data(), ar.host.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = alloc(&bs->nodes, rs * N3 * bs->G);
-  if (e == cudaSuccess) e = alloc(&bs->unodes, rs * N3 * bs->G);
-  if (e == cudaSuccess) e = alloc(&bs->fuser, rs * N3 * bs->B);
-  if (e == cudaSuccess) e = alloc(&bs->fwork, rs * N3 * bs->B);
-  if (e == cudaSuccess) e = alloc(&bs->wfield, rs * N3 * bs->B);
+  cudaError_t e = alloc((void**)&aar.dev, aar.host.size());
+  if (e == cudaSuccess) e = cudaMemcpy(aar.dev, aar.host.data(), aar.host.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = alloc(&bs->gseed, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->gW, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->gf, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->gtmp, rs * N3 * bs->B);
   if (e == cudaSuccess) e = alloc(&bs->aunodes, rs * N3 * bs->G);
   if (e == cudaSuccess) e = cudaMemset(bs->gseed, 0, rs * N3 * bs->B);
-  if (e == cudaSuccess) e = alloc(&bs->spec, 2 * rs * NW * bs->max_phase_blocks);
-  if (e == cudaSuccess) e = alloc(&bs->acc, 2 * rs * NW * bs->max_phase_blocks);
-  if (e == cudaSuccess) e = alloc(&bs->lap_in, rs * N3 * bs->max_level_blocks);
-  if (e == cudaSuccess) e = alloc(&bs->lap_out, rs * N3 * bs->max_level_blocks);
-  if (e == cudaSuccess) e = alloc((void**)&bs->d_err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(bs->fuser, 0, rs * N3 * bs->B);
-  if (e == cudaSuccess) e = cudaMemset(bs->unodes, 0, rs * N3 * bs->G);
-  if (e == cudaSuccess) e = cudaMemset(bs->d_err, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs->cstream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->ev_fuser_free, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->ev_loaded, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->ev_dev_load, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? FLGF_ENOMEM : FLGF_ECUDA;
-    return bail(code, std::string("blockset allocation: ") + cudaGetErrorString(e));
+    return fail(ctx, code, std::string("adjoint allocation: ") + cudaGetErrorString(e));
   }
-  *out = bs;
+  bs->adj_ready = true;
   return FLGF_OK;
 }
 
@@ -1159,11 +1204,10 @@ struct StageScope {
 // FMM of one phase: upward pass over `nodes`, forward FFTs, spectrum MAC,
 // inverse FFTs and downward pass into `unodes`.
 template <typename R>
-cudaError_t enqueue_fmm(flgf_blockset* bs, const PhaseOff& ph, R* unodes) {
+cudaError_t enqueue_fmm(flgf_blockset* bs, const Arena& ar, const PhaseOff& ph, R* unodes) {
   flgf_ctx* c = bs->ctx;
   const int N = c->N;
   cudaStream_t s = c->stream;
-  const Arena& ar = bs->ar;
   R* nodes = (R*)bs->nodes;
   cudaError_t e;
 #define KRUN(n, x)                              \
@@ -1217,7 +1261,8 @@ cudaError_t enqueue_adjoint(flgf_blockset* bs) {
   flgf_ctx* c = bs->ctx;
   const int N = c->N;
   cudaStream_t s = c->stream;
-  const Arena& ar = bs->ar;
+  const Arena& ar = bs->ar;   // forward lists (coarsening)
+  const Arena& aa = bs->aar;  // adjoint lists
   const size_t N3 = (size_t)N * N * N;
   R* nodes = (R*)bs->nodes;
   R* unodes = (R*)bs->aunodes;
@@ -1241,21 +1286,21 @@ cudaError_t enqueue_adjoint(flgf_blockset* bs) {
     {
       StageScope sc(bs, 6);
       if (bs->correction)
-        KRUN(ao.n_cf1, launch_cf_interp_adjoint<R>(N, gW, ar.at<int>(ao.cf1_nbr), gf, ar.at<int>(ao.cf1_fine),
-                                                   ar.at<int>(ao.cf1_cpos), ao.n_cf1, 1, ar.at<double>(ao.cf1_ih2),
+        KRUN(ao.n_cf1, launch_cf_interp_adjoint<R>(N, gW, aa.at<int>(ao.cf1_nbr), gf, aa.at<int>(ao.cf1_fine),
+                                                   aa.at<int>(ao.cf1_cpos), ao.n_cf1, 1, aa.at<double>(ao.cf1_ih2),
                                                    bs->d_err, s));
-      KRUN(ao.n_prep, launch_combine_blocks<R>(N, nodes, ar.at<int>(ao.prep_dst), gseed, ar.at<int>(ao.prep_s1), gW,
-                                               ar.at<int>(ao.prep_s2), 0, ao.n_prep, s));
+      KRUN(ao.n_prep, launch_combine_blocks<R>(N, nodes, aa.at<int>(ao.prep_dst), gseed, aa.at<int>(ao.prep_s1), gW,
+                                               aa.at<int>(ao.prep_s2), 0, ao.n_prep, s));
     }
-    if ((e = enqueue_fmm<R>(bs, bs->aph[l], unodes)) != cudaSuccess) return e;
+    if ((e = enqueue_fmm<R>(bs, aa, bs->aph[l], unodes)) != cudaSuccess) return e;
     {
       StageScope sc(bs, 6);
-      KRUN(ao.n_gacc, launch_combine_blocks<R>(N, gf, ar.at<int>(ao.gacc_dst), unodes, ar.at<int>(ao.gacc_s1), unodes,
-                                               ar.at<int>(ao.gacc_s2), 1, ao.n_gacc, s));
-      KRUN(ao.n_gtmp, launch_combine_blocks<R>(N, gtmp, ar.at<int>(ao.gtmp_dst), gseed, ar.at<int>(ao.gtmp_s1), gW,
-                                               ar.at<int>(ao.gtmp_s2), 0, ao.n_gtmp, s));
-      KRUN(ao.n_cf0, launch_cf_interp_adjoint<R>(N, gW, ar.at<int>(ao.cf0_nbr), gtmp, ar.at<int>(ao.cf0_fine),
-                                                 ar.at<int>(ao.cf0_cpos), ao.n_cf0, 0, nullptr, bs->d_err, s));
+      KRUN(ao.n_gacc, launch_combine_blocks<R>(N, gf, aa.at<int>(ao.gacc_dst), unodes, aa.at<int>(ao.gacc_s1), unodes,
+                                               aa.at<int>(ao.gacc_s2), 1, ao.n_gacc, s));
+      KRUN(ao.n_gtmp, launch_combine_blocks<R>(N, gtmp, aa.at<int>(ao.gtmp_dst), gseed, aa.at<int>(ao.gtmp_s1), gW,
+                                               aa.at<int>(ao.gtmp_s2), 0, ao.n_gtmp, s));
+      KRUN(ao.n_cf0, launch_cf_interp_adjoint<R>(N, gW, aa.at<int>(ao.cf0_nbr), gtmp, aa.at<int>(ao.cf0_fine),
+                                                 aa.at<int>(ao.cf0_cpos), ao.n_cf0, 0, nullptr, bs->d_err, s));
     }
   }
   {
@@ -1306,7 +1351,7 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
       KRUN(ph.n_prep, launch_copy_blocks<R>(N, fwork, ar.at<int>(ph.prep_src), nodes, ar.at<int>(ph.prep_dst),
                                             ar.at<uint8_t>(ph.prep_zero), ph.n_prep, s));
     }
-    if ((e = enqueue_fmm<R>(bs, ph, unodes)) != cudaSuccess) return e;
+    if ((e = enqueue_fmm<R>(bs, bs->ar, ph, unodes)) != cudaSuccess) return e;
     {
       StageScope sc(bs, 6);
       R* wf = (R*)bs->wfield;
@@ -1445,6 +1490,10 @@ extern "C" int flgf_load_adjoint(flgf_blockset* bs, int problem, int level, cons
   if (!bs || !g || (where != FLGF_HOST && where != FLGF_DEVICE)) return FLGF_EINVAL;
   flgf_ctx* ctx = bs->ctx;
   if (check_pl(bs, problem, level) != FLGF_OK) return fail(ctx, FLGF_EINVAL, "load_adjoint: bad problem/level");
+  if (!bs->adj_ready) {
+    const int rc = build_adjoint(bs);
+    if (rc != FLGF_OK) return rc;
+  }
   const LevelInfo& L = bs->prob[problem].lev[level];
   const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4, N3 = (size_t)ctx->N * ctx->N * ctx->N;
   CK(cudaMemcpyAsync((char*)bs->gseed + rs * N3 * L.fw0, g, rs * N3 * L.c.size(), kind(where, true), ctx->stream));
@@ -1455,6 +1504,10 @@ extern "C" int flgf_load_adjoint(flgf_blockset* bs, int problem, int level, cons
 extern "C" int flgf_solve_adjoint(flgf_blockset* bs) {
   if (!bs) return FLGF_EINVAL;
   flgf_ctx* ctx = bs->ctx;
+  if (!bs->adj_ready) {
+    const int rc = build_adjoint(bs);
+    if (rc != FLGF_OK) return rc;
+  }
   collect_times(bs);
   bs->ev_used = 0;
   cudaError_t e = ctx->prec == FLGF_FP64 ? enqueue_adjoint<double>(bs) : enqueue_adjoint<float>(bs);
