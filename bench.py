@@ -53,6 +53,8 @@ def args_parse():
     ap.add_argument("--precisions", default="fp32,fp64", help="contexts to time (profiling runs use fp32)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched leg")
+    ap.add_argument("--plan", default=None,
+                    help="fixed MAC plan for the batched leg, e.g. 30/4x4x4 (list percentage / tile); default: autotune")
     return ap.parse_args()
 
 
@@ -271,6 +273,10 @@ def run_ours(a, rank, world, dist):
         plan = None
         for prec in precs:
             bctx = F.Context(N=16, n_interp=6, precision=prec)
+            if plan is None and a.plan:
+                pct, tile = a.plan.split("/")
+                plan = (int(pct), tuple(int(v) for v in tile.split("x")))
+                batched["plan"] = {"list_pct": plan[0], "tile": list(plan[1]), "source": "--plan"}
             if plan is None:
                 # pick the MAC plan (dense tile, pair-list threshold) on this mesh
                 from paper_1911_10228_gb300.autotune import autotune
