@@ -216,20 +216,23 @@ __global__ void coarsen_kernel(int N, const R* __restrict__ fine_f, const int* _
 
 // Quadratic cell-centred weights on coarse cells (i-1, i, i+1) for the fine
 // cell at -1/4 (sub = 0) and +1/4 (sub = 1) of coarse cell i.
-__device__ __forceinline__ double cf_w(int sub, int e) {
-  const double w0[3] = {5.0 / 32.0, 15.0 / 16.0, -3.0 / 32.0};
-  return sub == 0 ? w0[e] : w0[2 - e];
+template <typename R>
+__device__ __forceinline__ R cf_w(int sub, int e) {  // exact in FP32 and FP64
+  const int i = sub == 0 ? e : 2 - e;
+  return i == 0 ? R(5.0 / 32.0) : (i == 1 ? R(15.0 / 16.0) : R(-3.0 / 32.0));
 }
 
-template <typename R>
-__global__ void cf_interp_kernel(int N, const R* __restrict__ ucoarse, const int* __restrict__ nbr27,
-                                 const int* __restrict__ fine_ids, const int* __restrict__ cposv,
-                                 R* __restrict__ fine, int mode, const double* __restrict__ inv_hf2, int* err_flag) {
+template <typename R, int N, int MODE>
+__global__ void __launch_bounds__(N >= 16 ? 256 : 128)
+    cf_interp_kernel(const R* __restrict__ ucoarse, const int* __restrict__ nbr27, const int* __restrict__ fine_ids,
+                     const int* __restrict__ cposv, R* __restrict__ fine, const double* __restrict__ inv_hf2,
+                     int* err_flag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N3 = N * N * N;
-  const int halo = mode == 1 ? 1 : 0;
-  const int F = N + 2 * halo;       // fine region extent
-  const int M = N / 2 + 2 + 2 * halo;  // coarse region extent
+  constexpr int mode = MODE;
+  constexpr int N3 = N * N * N;
+  constexpr int halo = mode == 1 ? 1 : 0;
+  constexpr int F = N + 2 * halo;          // fine region extent
+  constexpr int M = N / 2 + 2 + 2 * halo;  // coarse region extent
   R* C = reinterpret_cast<R*>(smem_raw);  // [M][M][M]
   R* T1 = C + M * M * M;                  // [M][M][F]
   R* T2 = T1 + M * M * F;                 // [M][F][F]
@@ -265,7 +268,7 @@ __global__ void cf_interp_kernel(int N, const R* __restrict__ ucoarse, const int
     const int g = o % F, ij = o / F;
     const int G = cp[2] * N + g - halo, ci = (G >> 1) - cbase[2], sub = G & 1;
     R s = 0;
-    for (int e = 0; e < 3; ++e) s += (R)cf_w(sub, e) * C[ij * M + ci + e - 1];
+    for (int e = 0; e < 3; ++e) s += cf_w<R>(sub, e) * C[ij * M + ci + e - 1];
     T1[o] = s;
   }
   __syncthreads();
@@ -273,7 +276,7 @@ __global__ void cf_interp_kernel(int N, const R* __restrict__ ucoarse, const int
     const int k = o % F, g = (o / F) % F, i = o / (F * F);
     const int G = cp[1] * N + g - halo, ci = (G >> 1) - cbase[1], sub = G & 1;
     R s = 0;
-    for (int e = 0; e < 3; ++e) s += (R)cf_w(sub, e) * T1[(i * M + ci + e - 1) * F + k];
+    for (int e = 0; e < 3; ++e) s += cf_w<R>(sub, e) * T1[(i * M + ci + e - 1) * F + k];
     T2[o] = s;
   }
   __syncthreads();
@@ -281,7 +284,7 @@ __global__ void cf_interp_kernel(int N, const R* __restrict__ ucoarse, const int
     const int jk = o % (F * F), g = o / (F * F);
     const int G = cp[0] * N + g - halo, ci = (G >> 1) - cbase[0], sub = G & 1;
     R s = 0;
-    for (int e = 0; e < 3; ++e) s += (R)cf_w(sub, e) * T2[(ci + e - 1) * F * F + jk];
+    for (int e = 0; e < 3; ++e) s += cf_w<R>(sub, e) * T2[(ci + e - 1) * F * F + jk];
     U[o] = s;
   }
   __syncthreads();
@@ -326,16 +329,17 @@ __global__ void combine_blocks_kernel(int N, R* __restrict__ dst, const int* __r
 // back through the tensor-product quadratic weights onto the coarse region of
 // the parent's 3x3x3 neighbourhood and added to the coarse field with atomics
 // (neighbouring fine blocks share coarse cells).
-template <typename R>
-__global__ void cf_interp_adjoint_kernel(int N, R* __restrict__ gcoarse, const int* __restrict__ nbr27,
-                                         const R* __restrict__ gfine, const int* __restrict__ fine_ids,
-                                         const int* __restrict__ cposv, int mode, const double* __restrict__ inv_hf2,
-                                         int* err_flag) {
+template <typename R, int N, int MODE>
+__global__ void __launch_bounds__(N >= 16 ? 256 : 128)
+    cf_interp_adjoint_kernel(R* __restrict__ gcoarse, const int* __restrict__ nbr27, const R* __restrict__ gfine,
+                             const int* __restrict__ fine_ids, const int* __restrict__ cposv,
+                             const double* __restrict__ inv_hf2, int* err_flag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N3 = N * N * N;
-  const int halo = mode == 1 ? 1 : 0;
-  const int F = N + 2 * halo;
-  const int M = N / 2 + 2 + 2 * halo;
+  constexpr int mode = MODE;
+  constexpr int N3 = N * N * N;
+  constexpr int halo = mode == 1 ? 1 : 0;
+  constexpr int F = N + 2 * halo;
+  constexpr int M = N / 2 + 2 + 2 * halo;
   R* C = reinterpret_cast<R*>(smem_raw);  // [M][M][M]
   R* T1 = C + M * M * M;                  // [M][M][F]
   R* T2 = T1 + M * M * F;                 // [M][F][F]
@@ -366,7 +370,7 @@ __global__ void cf_interp_adjoint_kernel(int N, R* __restrict__ gcoarse, const i
     R s = 0;
     for (int gg = 0; gg < F; ++gg) {
       const int G = cp[0] * N + gg - halo, e = ci - ((G >> 1) - cbase[0]) + 1;
-      if (e >= 0 && e < 3) s += (R)cf_w(G & 1, e) * U[gg * F * F + jk];
+      if (e >= 0 && e < 3) s += cf_w<R>(G & 1, e) * U[gg * F * F + jk];
     }
     T2[o] = s;
   }
@@ -376,7 +380,7 @@ __global__ void cf_interp_adjoint_kernel(int N, R* __restrict__ gcoarse, const i
     R s = 0;
     for (int gg = 0; gg < F; ++gg) {
       const int G = cp[1] * N + gg - halo, e = cj - ((G >> 1) - cbase[1]) + 1;
-      if (e >= 0 && e < 3) s += (R)cf_w(G & 1, e) * T2[(i * F + gg) * F + k];
+      if (e >= 0 && e < 3) s += cf_w<R>(G & 1, e) * T2[(i * F + gg) * F + k];
     }
     T1[o] = s;
   }
@@ -386,7 +390,7 @@ __global__ void cf_interp_adjoint_kernel(int N, R* __restrict__ gcoarse, const i
     R s = 0;
     for (int gg = 0; gg < F; ++gg) {
       const int G = cp[2] * N + gg - halo, e = ck - ((G >> 1) - cbase[2]) + 1;
-      if (e >= 0 && e < 3) s += (R)cf_w(G & 1, e) * T1[ij * F + gg];
+      if (e >= 0 && e < 3) s += cf_w<R>(G & 1, e) * T1[ij * F + gg];
     }
     C[o] = s;
   }
@@ -542,9 +546,17 @@ cudaError_t launch_cf_interp(int N, const R* ucoarse, const int* nbr27, const in
   const int halo = mode == 1 ? 1 : 0;
   const int F = N + 2 * halo, M = N / 2 + 2 + 2 * halo;
   const size_t sm = sizeof(R) * ((size_t)M * M * M + M * M * F + M * F * F + F * F * F);
-  cudaError_t e = set_smem(cf_interp_kernel<R>, sm);
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = set_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<n, threads_for(N), sm, s>>>(ucoarse, nbr27, fine_ids, cpos, fine, inv_hf2, err_flag);
+    return cudaSuccess;
+  };
+  cudaError_t e;
+  if (N == 16) e = mode ? go(cf_interp_kernel<R, 16, 1>) : go(cf_interp_kernel<R, 16, 0>);
+  else if (N == 8) e = mode ? go(cf_interp_kernel<R, 8, 1>) : go(cf_interp_kernel<R, 8, 0>);
+  else return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
-  cf_interp_kernel<R><<<n, threads_for(N), sm, s>>>(N, ucoarse, nbr27, fine_ids, cpos, fine, mode, inv_hf2, err_flag);
   return cudaGetLastError();
 }
 
@@ -564,10 +576,17 @@ cudaError_t launch_cf_interp_adjoint(int N, R* gcoarse, const int* nbr27, const 
   const int halo = mode == 1 ? 1 : 0;
   const int F = N + 2 * halo, M = N / 2 + 2 + 2 * halo;
   const size_t sm = sizeof(R) * ((size_t)M * M * M + M * M * F + M * F * F + F * F * F);
-  cudaError_t e = set_smem(cf_interp_adjoint_kernel<R>, sm);
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = set_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<n, threads_for(N), sm, s>>>(gcoarse, nbr27, gfine, fine_ids, cpos, inv_hf2, err_flag);
+    return cudaSuccess;
+  };
+  cudaError_t e;
+  if (N == 16) e = mode ? go(cf_interp_adjoint_kernel<R, 16, 1>) : go(cf_interp_adjoint_kernel<R, 16, 0>);
+  else if (N == 8) e = mode ? go(cf_interp_adjoint_kernel<R, 8, 1>) : go(cf_interp_adjoint_kernel<R, 8, 0>);
+  else return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
-  cf_interp_adjoint_kernel<R><<<n, threads_for(N), sm, s>>>(N, gcoarse, nbr27, gfine, fine_ids, cpos, mode, inv_hf2,
-                                                            err_flag);
   return cudaGetLastError();
 }
 
