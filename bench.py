@@ -53,6 +53,7 @@ def args_parse():
     ap.add_argument("--precisions", default="fp32,fp64", help="contexts to time (profiling runs use fp32)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched leg")
+    ap.add_argument("--no-multires", action="store_true", help="skip the refined-mesh and adjoint legs")
     ap.add_argument("--plan", default=None,
                     help="fixed MAC plan for the batched leg, e.g. 30/4x4x4 (list percentage / tile); default: autotune")
     return ap.parse_args()
@@ -326,6 +327,76 @@ def run_ours(a, rank, world, dist):
             batched["fp32_vs_fp64_linf"] = num / den
         del outs
 
+    # refined meshes: the 3-level torus (FP32 and FP64, graph-replayed) and the
+    # adjoint (gradient) solve on the linked tori, FP32
+    multires, adjoint = None, None
+    if not a.no_multires:
+        from paper_1911_10228_gb300.inputs import config_linked_tori, config_torus_128
+
+        def timed(stream, fn, n):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+            MR.barrier("cuda")
+            torch.cuda.synchronize()
+            sampler.start()
+            for s0, s1 in ev:
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                s0.record(stream)
+                fn()
+                s1.record(stream)
+            torch.cuda.synchronize()
+            sampler.stop()
+            MR.barrier("cuda")
+            return MR.all_max(float(np.mean([s0.elapsed_time(s1) for s0, s1 in ev])), "cuda")
+
+        tp = config_torus_128()
+        tdof = tp.dof()
+        multires = {"workload": "Gaussian-core torus (R 0.25, sigma 0.03), base 128^3 in 8^3 blocks of 16^3, 3 levels "
+                                "refined where |f| > 1e-3 max, n_I=6, source correction on, CUDA graph",
+                    "dof": tdof, "blocks": int(sum(len(c) for c in tp.coords))}
+        outs = {}
+        for prec in precs:
+            mctx = F.Context(N=16, n_interp=6, precision=prec)
+            mbs = F.BlockSet(mctx, [tp.coords], [tp.h0])
+            for l, f in enumerate(tp.f):
+                mbs.load_source(0, l, torch.as_tensor(f))
+            mbs.set_option(F.OPT_GRAPH, 1)
+            for _ in range(max(1, a.warmup)):
+                mbs.solve()
+            n = a.steps if prec == "fp32" else 2
+            ms = timed(mctx.stream, mbs.solve, n)
+            multires[prec] = {"value": tdof * world / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "steps": n,
+                              "launches_per_step": mbs.launch_count()}
+            outs[prec] = [mbs.potential(0, l) for l in range(tp.n_levels)]
+            mbs.close()
+            mctx.close()
+        if "fp64" in outs:
+            lm = tp.leaf_masks()
+            num = max(float((x.double() - y)[torch.as_tensor(m, device=y.device)].abs().max())
+                      for x, y, m in zip(outs["fp32"], outs["fp64"], lm))
+            den = max(float(y[torch.as_tensor(m, device=y.device)].abs().max()) for y, m in zip(outs["fp64"], lm))
+            multires["fp32_vs_fp64_linf"] = num / den
+        del outs
+        lt = config_linked_tori()
+        ldof = lt.dof()
+        actx = F.Context(N=16, n_interp=6, precision="fp32")
+        abs_ = F.BlockSet(actx, [lt.coords], [lt.h0])
+        rng = np.random.default_rng(0)
+        for l, f in enumerate(lt.f):
+            abs_.load_source(0, l, torch.as_tensor(f))
+            abs_.load_adjoint(0, l, torch.as_tensor(rng.standard_normal(f.shape).astype(np.float32)))
+        abs_.solve()
+        for _ in range(max(1, a.warmup)):
+            abs_.solve_adjoint()
+        n = min(a.steps, 10)
+        ms = timed(actx.stream, abs_.solve_adjoint, n)
+        adjoint = {"workload": "linked Gaussian tori (R 0.2, sigma 0.03), base 128^3 in 8^3 blocks of 16^3, 3 levels "
+                               "(512^3-equivalent finest level), FP32, source correction on: A^T g for random seeds",
+                   "dof": ldof, "value": ldof * world / (ms / 1e3), "unit": "DoF/s (gradient)", "ms_per_step": ms,
+                   "steps": n, "launches_per_step": abs_.launch_count()}
+        abs_.close()
+        actx.close()
+
     # end-to-end FP32 through the public API with pinned host buffers
     r32 = res["fp32"]
     bs = r32["bs"]
@@ -432,6 +503,8 @@ def run_ours(a, rank, world, dist):
                         "fft_inverse_frac": rows["fp32"]["fft_inv_gbs"] / hbm},
         "stages_ms": res["fp32"]["stages_ms"],
         "batched": batched,
+        "multires": multires,
+        "adjoint": adjoint,
         "cpu_baseline": cpu,
         "e2e": None if e2e_ms_step is None else {
             "value": dof * world / (e2e_ms_step / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": nbytes,
