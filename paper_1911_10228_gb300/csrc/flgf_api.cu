@@ -2,6 +2,8 @@
 // block-set compilation (mesh checks, octrees, interaction tiles, launch
 // lists) and the solve sequence of Sec. 2.1 / Sec. 3.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -433,6 +435,155 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
   // targets of sparse tiles per octree level, in tile order: (target id, pair list)
   std::vector<std::vector<std::pair<int, std::vector<int>>>> lpool;
   const int nchunk = ctx->prec == FLGF_FP64 ? nchunks<double>(N) : nchunks<float>(N);
+  // interaction tiles of one (instance, octree level): the expensive part of
+  // list building, run on the host's cores (see below)
+  struct TileJob {
+    const Inst* inp;
+    int k;
+    std::vector<ParentRec> drecs;                           // parents of dense tiles, in tile order
+    std::vector<std::pair<int, std::vector<int>>> lrecs;   // targets of sparse tiles with their pair lists
+    int64_t pairs = 0;
+  };
+  std::vector<TileJob> jobs;
+  auto run_tiles = [&](TileJob& job) {
+    const Inst& in = *job.inp;
+    const size_t k = (size_t)job.k;
+    // interaction tiles of this octree level
+    I3 lo = {INT32_MAX, INT32_MAX, INT32_MAX}, hi = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (const auto& c : in.lv[k])
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], c[a] >> 1);
+        hi[a] = std::max(hi[a], c[a] >> 1);
+      }
+    // block index by coordinates: a dense grid over the level's box when it is
+    // small enough (every lookup below stays inside [2 lo, 2 hi + 1]), else the hash map
+    const I3 glo = {2 * lo[0], 2 * lo[1], 2 * lo[2]};
+    const int64_t gd[3] = {2 * (int64_t)(hi[0] - lo[0]) + 2, 2 * (int64_t)(hi[1] - lo[1]) + 2,
+                           2 * (int64_t)(hi[2] - lo[2]) + 2};
+    const bool use_grid = gd[0] * gd[1] * gd[2] <= ((int64_t)1 << 24);
+    std::vector<int> grid;
+    if (use_grid) {
+      grid.assign((size_t)(gd[0] * gd[1] * gd[2]), -1);
+      for (size_t i = 0; i < in.lv[k].size(); ++i) {
+        const I3& c = in.lv[k][i];
+        grid[((size_t)(c[0] - glo[0]) * gd[1] + (c[1] - glo[1])) * gd[2] + (c[2] - glo[2])] = (int)i;
+      }
+    }
+    auto lookup = [&](int a, int b, int c2) -> int {
+      if (use_grid) {
+        const int64_t x = a - glo[0], y = b - glo[1], z = c2 - glo[2];
+        if (x < 0 || y < 0 || z < 0 || x >= gd[0] || y >= gd[1] || z >= gd[2]) return -1;
+        return grid[((size_t)x * gd[1] + y) * gd[2] + z];
+      }
+      auto it = in.idx[k].find(key3(a, b, c2));
+      return it == in.idx[k].end() ? -1 : it->second;
+    };
+    const bool excl = k > 0;
+    for (int t0 = lo[0]; t0 <= hi[0]; t0 += TP[0])
+      for (int t1 = lo[1]; t1 <= hi[1]; t1 += TP[1])
+        for (int t2 = lo[2]; t2 <= hi[2]; t2 += TP[2]) {
+          struct { int P[3], r0[3], Rg[3]; } tl;  // tile and its region (tile + 1 parent, clipped)
+          const int t[3] = {t0, t1, t2};
+          for (int a = 0; a < 3; ++a) {
+            tl.P[a] = std::min(TP[a], hi[a] - t[a] + 1);
+            tl.r0[a] = std::max(t[a] - 1, lo[a]);
+            tl.Rg[a] = std::min(t[a] + tl.P[a], hi[a]) - tl.r0[a] + 1;
+          }
+          std::vector<int> tg;
+          bool any = false;
+          for (int x = 0; x < 2 * tl.P[0]; ++x)
+            for (int y = 0; y < 2 * tl.P[1]; ++y)
+              for (int z = 0; z < 2 * tl.P[2]; ++z) {
+                const int i = lookup(2 * t0 + x, 2 * t1 + y, 2 * t2 + z);
+                const bool need = i >= 0 && in.need_tgt[k][i];
+                tg.push_back(need ? in.gid0[k] + i - ph.gid_begin : -1);
+                any |= need;
+              }
+          if (!any) continue;
+          // source slots in parity-major order: slot = b * NQ + q
+          const int NQ = tl.Rg[0] * tl.Rg[1] * tl.Rg[2];
+          std::vector<int> sg(8 * NQ, -1);
+          for (int x = 0; x < 2 * tl.Rg[0]; ++x)
+            for (int y = 0; y < 2 * tl.Rg[1]; ++y)
+              for (int z = 0; z < 2 * tl.Rg[2]; ++z) {
+                const int i = lookup(2 * tl.r0[0] + x, 2 * tl.r0[1] + y, 2 * tl.r0[2] + z);
+                const int b = ((x & 1) << 2) | ((y & 1) << 1) | (z & 1);
+                const int qq = ((x >> 1) * tl.Rg[1] + (y >> 1)) * tl.Rg[2] + (z >> 1);
+                sg[b * NQ + qq] = i >= 0 && in.is_src[k][i] ? in.gid0[k] + i - ph.gid_begin : -1;
+              }
+          // the interacting (target, source) pairs of every target: the
+          // candidates are the children of its parent's 27 neighbours
+          std::vector<std::vector<int>> plist(tg.size());  // (source id << 9) | offset index
+          int64_t useful = 0;
+          for (int x = 0; x < 2 * tl.P[0]; ++x)
+            for (int y = 0; y < 2 * tl.P[1]; ++y)
+              for (int z = 0; z < 2 * tl.P[2]; ++z) {
+                const int ti = (x * 2 * tl.P[1] + y) * 2 * tl.P[2] + z;
+                if (tg[ti] < 0) continue;
+                const int tc[3] = {2 * t0 + x, 2 * t1 + y, 2 * t2 + z};
+                for (int e = 0; e < 27; ++e)
+                  for (int b = 0; b < 8; ++b) {
+                    const int sc[3] = {2 * ((tc[0] >> 1) + e / 9 - 1) + (b >> 2),
+                                       2 * ((tc[1] >> 1) + (e / 3) % 3 - 1) + ((b >> 1) & 1),
+                                       2 * ((tc[2] >> 1) + e % 3 - 1) + (b & 1)};
+                    int rr[3];
+                    bool in = true, near = true;
+                    for (int a = 0; a < 3; ++a) {
+                      rr[a] = sc[a] - 2 * tl.r0[a];
+                      in &= rr[a] >= 0 && rr[a] < 2 * tl.Rg[a];
+                      near &= std::abs(sc[a] - tc[a]) <= 1;
+                    }
+                    if (!in || (excl && near)) continue;
+                    const int bb = ((rr[0] & 1) << 2) | ((rr[1] & 1) << 1) | (rr[2] & 1);
+                    const int qq = ((rr[0] >> 1) * tl.Rg[1] + (rr[1] >> 1)) * tl.Rg[2] + (rr[2] >> 1);
+                    const int sid = sg[bb * NQ + qq];
+                    if (sid < 0) continue;
+                    plist[ti].push_back((sid << 9) | off_index(tc[0] - sc[0], tc[1] - sc[1], tc[2] - sc[2]));
+                  }
+                useful += (int64_t)plist[ti].size();
+              }
+          job.pairs += useful;
+          // parent records of the tile's parents that have targets
+          std::vector<ParentRec> recs;
+          int64_t dense = 0;  // complex MACs per frequency of the parent-group kernel
+          for (int p0 = 0; p0 < tl.P[0]; ++p0)
+            for (int p1 = 0; p1 < tl.P[1]; ++p1)
+              for (int p2 = 0; p2 < tl.P[2]; ++p2) {
+                ParentRec r;
+                bool has = false;
+                for (int a = 0; a < 8; ++a) {
+                  r.tgt[a] = tg[((2 * p0 + (a >> 2)) * 2 * tl.P[1] + 2 * p1 + ((a >> 1) & 1)) * 2 * tl.P[2] + 2 * p2 +
+                                (a & 1)];
+                  has |= r.tgt[a] >= 0;
+                }
+                if (!has) continue;
+                const int pc[3] = {t0 + p0, t1 + p1, t2 + p2};
+                for (int e = 0; e < 27; ++e) {
+                  const int ee[3] = {e / 9 - 1, (e / 3) % 3 - 1, e % 3 - 1};
+                  int q[3];
+                  bool inr = !(excl && e == 13);
+                  for (int a = 0; a < 3; ++a) {
+                    q[a] = pc[a] + ee[a] - tl.r0[a];
+                    inr &= q[a] >= 0 && q[a] < tl.Rg[a];
+                  }
+                  bool any_src = false;
+                  for (int b = 0; b < 8; ++b) {
+                    r.cell[e][b] = inr ? sg[b * NQ + (q[0] * tl.Rg[1] + q[1]) * tl.Rg[2] + q[2]] : -1;
+                    any_src |= r.cell[e][b] >= 0;
+                  }
+                  dense += any_src ? 64 : 0;
+                }
+                recs.push_back(r);
+              }
+          if (useful * 100 < (int64_t)ctx->list_pct * dense) {
+            // sparse tile: its targets join the pair-list pool of octree level k
+            for (int ti = 0; ti < (int)tg.size(); ++ti)
+              if (tg[ti] >= 0) job.lrecs.push_back({tg[ti], std::move(plist[ti])});
+            continue;
+          }
+          job.drecs.insert(job.drecs.end(), recs.begin(), recs.end());
+        }
+  };
   for (const Inst* inp : insts) {
     const Inst& in = *inp;
     const LevelInfo& L = bs->prob[in.p].lev[l];
@@ -472,143 +623,32 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
           }
         }
       }
-      // interaction tiles of this octree level
-      I3 lo = {INT32_MAX, INT32_MAX, INT32_MAX}, hi = {INT32_MIN, INT32_MIN, INT32_MIN};
-      for (const auto& c : in.lv[k])
-        for (int a = 0; a < 3; ++a) {
-          lo[a] = std::min(lo[a], c[a] >> 1);
-          hi[a] = std::max(hi[a], c[a] >> 1);
-        }
-      // block index by coordinates: a dense grid over the level's box when it is
-      // small enough (every lookup below stays inside [2 lo, 2 hi + 1]), else the hash map
-      const I3 glo = {2 * lo[0], 2 * lo[1], 2 * lo[2]};
-      const int64_t gd[3] = {2 * (int64_t)(hi[0] - lo[0]) + 2, 2 * (int64_t)(hi[1] - lo[1]) + 2,
-                             2 * (int64_t)(hi[2] - lo[2]) + 2};
-      const bool dense = gd[0] * gd[1] * gd[2] <= ((int64_t)1 << 24);
-      std::vector<int> grid;
-      if (dense) {
-        grid.assign((size_t)(gd[0] * gd[1] * gd[2]), -1);
-        for (size_t i = 0; i < in.lv[k].size(); ++i) {
-          const I3& c = in.lv[k][i];
-          grid[((size_t)(c[0] - glo[0]) * gd[1] + (c[1] - glo[1])) * gd[2] + (c[2] - glo[2])] = (int)i;
-        }
-      }
-      auto lookup = [&](int a, int b, int c2) -> int {
-        if (dense) {
-          const int64_t x = a - glo[0], y = b - glo[1], z = c2 - glo[2];
-          if (x < 0 || y < 0 || z < 0 || x >= gd[0] || y >= gd[1] || z >= gd[2]) return -1;
-          return grid[((size_t)x * gd[1] + y) * gd[2] + z];
-        }
-        auto it = in.idx[k].find(key3(a, b, c2));
-        return it == in.idx[k].end() ? -1 : it->second;
-      };
-      const bool excl = k > 0;
-      for (int t0 = lo[0]; t0 <= hi[0]; t0 += TP[0])
-        for (int t1 = lo[1]; t1 <= hi[1]; t1 += TP[1])
-          for (int t2 = lo[2]; t2 <= hi[2]; t2 += TP[2]) {
-            struct { int P[3], r0[3], Rg[3]; } tl;  // tile and its region (tile + 1 parent, clipped)
-            const int t[3] = {t0, t1, t2};
-            for (int a = 0; a < 3; ++a) {
-              tl.P[a] = std::min(TP[a], hi[a] - t[a] + 1);
-              tl.r0[a] = std::max(t[a] - 1, lo[a]);
-              tl.Rg[a] = std::min(t[a] + tl.P[a], hi[a]) - tl.r0[a] + 1;
-            }
-            std::vector<int> tg;
-            bool any = false;
-            for (int x = 0; x < 2 * tl.P[0]; ++x)
-              for (int y = 0; y < 2 * tl.P[1]; ++y)
-                for (int z = 0; z < 2 * tl.P[2]; ++z) {
-                  const int i = lookup(2 * t0 + x, 2 * t1 + y, 2 * t2 + z);
-                  const bool need = i >= 0 && in.need_tgt[k][i];
-                  tg.push_back(need ? in.gid0[k] + i - ph.gid_begin : -1);
-                  any |= need;
-                }
-            if (!any) continue;
-            // source slots in parity-major order: slot = b * NQ + q
-            const int NQ = tl.Rg[0] * tl.Rg[1] * tl.Rg[2];
-            std::vector<int> sg(8 * NQ, -1);
-            for (int x = 0; x < 2 * tl.Rg[0]; ++x)
-              for (int y = 0; y < 2 * tl.Rg[1]; ++y)
-                for (int z = 0; z < 2 * tl.Rg[2]; ++z) {
-                  const int i = lookup(2 * tl.r0[0] + x, 2 * tl.r0[1] + y, 2 * tl.r0[2] + z);
-                  const int b = ((x & 1) << 2) | ((y & 1) << 1) | (z & 1);
-                  const int qq = ((x >> 1) * tl.Rg[1] + (y >> 1)) * tl.Rg[2] + (z >> 1);
-                  sg[b * NQ + qq] = i >= 0 && in.is_src[k][i] ? in.gid0[k] + i - ph.gid_begin : -1;
-                }
-            // the interacting (target, source) pairs of every target: the
-            // candidates are the children of its parent's 27 neighbours
-            std::vector<std::vector<int>> plist(tg.size());  // (source id << 9) | offset index
-            int64_t useful = 0;
-            for (int x = 0; x < 2 * tl.P[0]; ++x)
-              for (int y = 0; y < 2 * tl.P[1]; ++y)
-                for (int z = 0; z < 2 * tl.P[2]; ++z) {
-                  const int ti = (x * 2 * tl.P[1] + y) * 2 * tl.P[2] + z;
-                  if (tg[ti] < 0) continue;
-                  const int tc[3] = {2 * t0 + x, 2 * t1 + y, 2 * t2 + z};
-                  for (int e = 0; e < 27; ++e)
-                    for (int b = 0; b < 8; ++b) {
-                      const int sc[3] = {2 * ((tc[0] >> 1) + e / 9 - 1) + (b >> 2),
-                                         2 * ((tc[1] >> 1) + (e / 3) % 3 - 1) + ((b >> 1) & 1),
-                                         2 * ((tc[2] >> 1) + e % 3 - 1) + (b & 1)};
-                      int rr[3];
-                      bool in = true, near = true;
-                      for (int a = 0; a < 3; ++a) {
-                        rr[a] = sc[a] - 2 * tl.r0[a];
-                        in &= rr[a] >= 0 && rr[a] < 2 * tl.Rg[a];
-                        near &= std::abs(sc[a] - tc[a]) <= 1;
-                      }
-                      if (!in || (excl && near)) continue;
-                      const int bb = ((rr[0] & 1) << 2) | ((rr[1] & 1) << 1) | (rr[2] & 1);
-                      const int qq = ((rr[0] >> 1) * tl.Rg[1] + (rr[1] >> 1)) * tl.Rg[2] + (rr[2] >> 1);
-                      const int sid = sg[bb * NQ + qq];
-                      if (sid < 0) continue;
-                      plist[ti].push_back((sid << 9) | off_index(tc[0] - sc[0], tc[1] - sc[1], tc[2] - sc[2]));
-                    }
-                  useful += (int64_t)plist[ti].size();
-                }
-            if (count) bs->pairs += useful;
-            // parent records of the tile's parents that have targets
-            std::vector<ParentRec> recs;
-            int64_t dense = 0;  // complex MACs per frequency of the parent-group kernel
-            for (int p0 = 0; p0 < tl.P[0]; ++p0)
-              for (int p1 = 0; p1 < tl.P[1]; ++p1)
-                for (int p2 = 0; p2 < tl.P[2]; ++p2) {
-                  ParentRec r;
-                  bool has = false;
-                  for (int a = 0; a < 8; ++a) {
-                    r.tgt[a] = tg[((2 * p0 + (a >> 2)) * 2 * tl.P[1] + 2 * p1 + ((a >> 1) & 1)) * 2 * tl.P[2] + 2 * p2 +
-                                  (a & 1)];
-                    has |= r.tgt[a] >= 0;
-                  }
-                  if (!has) continue;
-                  const int pc[3] = {t0 + p0, t1 + p1, t2 + p2};
-                  for (int e = 0; e < 27; ++e) {
-                    const int ee[3] = {e / 9 - 1, (e / 3) % 3 - 1, e % 3 - 1};
-                    int q[3];
-                    bool inr = !(excl && e == 13);
-                    for (int a = 0; a < 3; ++a) {
-                      q[a] = pc[a] + ee[a] - tl.r0[a];
-                      inr &= q[a] >= 0 && q[a] < tl.Rg[a];
-                    }
-                    bool any_src = false;
-                    for (int b = 0; b < 8; ++b) {
-                      r.cell[e][b] = inr ? sg[b * NQ + (q[0] * tl.Rg[1] + q[1]) * tl.Rg[2] + q[2]] : -1;
-                      any_src |= r.cell[e][b] >= 0;
-                    }
-                    dense += any_src ? 64 : 0;
-                  }
-                  recs.push_back(r);
-                }
-            if (useful * 100 < (int64_t)ctx->list_pct * dense) {
-              // sparse tile: its targets join the pair-list pool of octree level k
-              if ((int)lpool.size() <= (int)k) lpool.resize(k + 1);
-              for (int ti = 0; ti < (int)tg.size(); ++ti)
-                if (tg[ti] >= 0) lpool[k].push_back({tg[ti], std::move(plist[ti])});
-              continue;
-            }
-            if ((int)dpool.size() <= (int)k) dpool.resize(k + 1);
-            dpool[k].insert(dpool[k].end(), recs.begin(), recs.end());
-          }
+      jobs.push_back(TileJob{&in, (int)k});
+    }
+  }
+  // run the tile jobs on the host's cores; the results are merged in job order,
+  // so the launch lists do not depend on the number of threads
+  {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const size_t nth = std::min<size_t>(jobs.size(), std::max(1u, std::min(hw, 32u)));
+    std::atomic<size_t> next{0};
+    auto worker = [&]() {
+      for (size_t j = next++; j < jobs.size(); j = next++) run_tiles(jobs[j]);
+    };
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < nth; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+  }
+  for (TileJob& job : jobs) {
+    if (count) bs->pairs += job.pairs;
+    if (!job.drecs.empty()) {
+      if ((int)dpool.size() <= job.k) dpool.resize(job.k + 1);
+      dpool[job.k].insert(dpool[job.k].end(), job.drecs.begin(), job.drecs.end());
+    }
+    if (!job.lrecs.empty()) {
+      if ((int)lpool.size() <= job.k) lpool.resize(job.k + 1);
+      for (auto& r : job.lrecs) lpool[job.k].push_back(std::move(r));
     }
   }
   // dense MAC: parent groups of every octree level
