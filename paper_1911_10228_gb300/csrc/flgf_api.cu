@@ -1,13 +1,14 @@
 // Host side of the FLGF library: context set-up (LGF table, kernel spectra),
-// block-set compilation (mesh checks, octrees, interaction tiles, launch
-// lists) and the solve sequence of Sec. 2.1 / Sec. 3.
+// block-set compilation (mesh checks, octrees, interaction tiles, parent groups
+// and pair lists, launch lists), the solve sequence of Sec. 2.1 / Sec. 3 and
+// its adjoint.
 #include <algorithm>
-#include <atomic>
-#include <thread>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
