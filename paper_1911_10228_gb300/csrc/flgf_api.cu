@@ -637,7 +637,13 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
       for (size_t j = next++; j < jobs.size(); j = next++) run_tiles(jobs[j]);
     };
     std::vector<std::thread> pool;
-    for (size_t t = 1; t < nth; ++t) pool.emplace_back(worker);
+    for (size_t t = 1; t < nth; ++t) {
+      try {
+        pool.emplace_back(worker);
+      } catch (...) {  // no more threads: the workers already started and this one finish the jobs
+        break;
+      }
+    }
     worker();
     for (auto& th : pool) th.join();
   }
@@ -1043,9 +1049,17 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
 static int build_adjoint(flgf_blockset* bs) {
   flgf_ctx* ctx = bs->ctx;
   const size_t N3 = (size_t)ctx->N * ctx->N * ctx->N;
+  // start from nothing, so a call after a failed one (out of memory) rebuilds cleanly
+  for (void** p : {&bs->gseed, &bs->gW, &bs->gf, &bs->gtmp, &bs->aunodes}) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  cudaFree(bs->aar.dev);
+  bs->aar = Arena();
+  bs->aph.assign(bs->Lmax, PhaseOff());
+  bs->adj.assign(bs->Lmax, AdjOff());
+  bs->adj_inst.clear();
   Arena& aar = bs->aar;
-  bs->aph.resize(bs->Lmax);
-  bs->adj.resize(bs->Lmax);
   bs->adj_inst.reserve(bs->inst.size());
   for (const auto& in : bs->inst) {
     if (in.variant != 1) continue;
