@@ -760,20 +760,14 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
   ph.inv_scale = ar.add(inv_scale);
 }
 
-extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
-                                    const int32_t* coords, const double* h0, flgf_blockset** out) {
-  if (!ctx || !out || n_problems < 1 || !n_levels || !nblk || !coords || !h0)
-    return fail(ctx, FLGF_EINVAL, "blockset_create: bad arguments");
-  *out = nullptr;
+// Mesh checks, octrees and launch lists of a block set: host work only (no
+// CUDA call), so the planning can be exercised without a GPU.  On failure the
+// caller destroys bs.
+static int plan_blockset(flgf_ctx* ctx, flgf_blockset* bs, int n_problems, const int* n_levels, const int* nblk,
+                         const int32_t* coords, const double* h0) {
   const int N = ctx->N;
   const size_t N3 = (size_t)N * N * N;
-  auto bs = new (std::nothrow) flgf_blockset();
-  if (!bs) return fail(ctx, FLGF_ENOMEM, "host allocation");
-  bs->ctx = ctx;
-  auto bail = [&](int code, const std::string& m) {
-    flgf_blockset_destroy(bs);
-    return fail(ctx, code, m);
-  };
+  auto bail = [&](int code, const std::string& m) { return fail(ctx, code, m); };
   // ---- read and validate the mesh ------------------------------------------
   int q = 0;
   size_t ci = 0;
@@ -1010,6 +1004,29 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
           }
       L.nbr6_off = ar.add(n6);
     }
+  return FLGF_OK;
+}
+
+extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
+                                    const int32_t* coords, const double* h0, flgf_blockset** out) {
+  if (!ctx || !out || n_problems < 1 || !n_levels || !nblk || !coords || !h0)
+    return fail(ctx, FLGF_EINVAL, "blockset_create: bad arguments");
+  *out = nullptr;
+  auto bs = new (std::nothrow) flgf_blockset();
+  if (!bs) return fail(ctx, FLGF_ENOMEM, "host allocation");
+  bs->ctx = ctx;
+  auto bail = [&](int code, const std::string& m) {
+    flgf_blockset_destroy(bs);
+    return fail(ctx, code, m);
+  };
+  const int rc = plan_blockset(ctx, bs, n_problems, n_levels, nblk, coords, h0);
+  if (rc != FLGF_OK) {
+    flgf_blockset_destroy(bs);
+    return rc;
+  }
+  const int N = ctx->N;
+  const size_t N3 = (size_t)N * N * N;
+  Arena& ar = bs->ar;
   // ---- device memory ---------------------------------------------------------
   const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4;
   const size_t NW = (size_t)nfreq(N);
