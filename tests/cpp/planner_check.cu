@@ -5,7 +5,8 @@
 // own octree level.  The expected pairs are enumerated from the interaction
 // rule directly: the children of the 27 neighbours of the target's parent that
 // are sources, the near ones (|t - s|_inf <= 1) only on the finest octree
-// level.  No CUDA call is made; the planning runs on the CPU.
+// level.  The forward phases and the adjoint phases (transposed leaf-only
+// instances) are checked.  The planning runs on the CPU.
 //
 // usage: planner_check <mesh file> <list_pct> <t0> <t1> <t2> <fp64 0|1>
 // mesh file (int32): N, n_problems, n_levels[n_problems], nblk[sum levels],
@@ -54,15 +55,14 @@ int main(int argc, char** argv) {
     printf("plan failed (%d): %s\n", rc, ctx.err.c_str());
     return 1;
   }
-  const char* base = bs->ar.host.data();
   long bad = 0, pairs = 0, dense_pairs = 0, list_pairs = 0;
-  for (int l = 0; l < bs->Lmax; ++l) {
-    const PhaseOff& ph = bs->ph[l];
+  // the launch lists of one phase (arena base) against the instances it serves
+  auto check_phase = [&](const PhaseOff& ph, const char* base, const std::vector<const Inst*>& insts) {
     using Pair = std::tuple<int, int, int>;  // target, source (phase-local columns), offset index
     std::map<Pair, int> want, got;
     std::map<int, int> tlevel, written;      // target -> octree level, and times it is written
-    for (const Inst& in : bs->inst) {
-      if (in.l != l) continue;
+    for (const Inst* inp : insts) {
+      const Inst& in = *inp;
       for (size_t k = 0; k < in.lv.size(); ++k)
         for (size_t i = 0; i < in.lv[k].size(); ++i) {
           if (!in.need_tgt[k][i]) continue;
@@ -143,6 +143,24 @@ int main(int argc, char** argv) {
     for (const auto& kv : want) bad += kv.second != 1 || got[kv.first] != 1;
     bad += got.size() != want.size();
     pairs += (long)want.size();
+  };
+  for (int l = 0; l < bs->Lmax; ++l) {  // forward phases
+    std::vector<const Inst*> insts;
+    for (const Inst& in : bs->inst)
+      if (in.l == l) insts.push_back(&in);
+    check_phase(bs->ph[l], bs->ar.host.data(), insts);
+  }
+  // adjoint phases: build_adjoint compiles the transposed lists first and then
+  // allocates device buffers, which fails without a GPU; the lists are complete
+  build_adjoint(bs);
+  for (int l = 0; l < bs->Lmax; ++l) {
+    std::vector<const Inst*> insts;
+    for (const Inst& in : bs->inst)
+      if (in.l == l && in.variant == 0) insts.push_back(&in);
+    for (const Inst& in : bs->adj_inst)
+      if (in.l == l) insts.push_back(&in);
+    if ((int)bs->aph.size() <= l) { ++bad; continue; }
+    check_phase(bs->aph[l], bs->aar.host.data(), insts);
   }
   printf("pairs %ld (dense kernel %ld, pair lists %ld) mismatches %ld\n", pairs, dense_pairs, list_pairs, bad);
   printf("%s\n", bad ? "FAILED" : "ok");
