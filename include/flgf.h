@@ -103,8 +103,20 @@ void flgf_destroy(flgf_ctx* ctx);
  *                      Tiles are the unit of the pair-list decision, and
  *                      their order is the order in which parents are packed
  *                      into the dense kernel's groups.
+ *   FLGF_CTX_ORDER     0 (default): the parents of each dense-kernel group keep
+ *                      the tile order; 1: they are ordered by their set of
+ *                      neighbours with sources (most first, equal sets
+ *                      together), so the threads of a warp skip the same
+ *                      absent neighbours (it loses the consecutive cell reads
+ *                      of the tile order; measured slower on the uniform and
+ *                      batched workloads, kept for the autotuner).
+ *   FLGF_CTX_FAIL_ALLOC failure injection for tests of the error paths: with
+ *                      value n >= 1 the n-th device allocation of the block
+ *                      sets of this context (counted from this call; creation
+ *                      and the adjoint's first use allocate) reports
+ *                      FLGF_ENOMEM without allocating; 0 disarms.  One shot.
  * FLGF_EINVAL for an unknown key or a value out of range. */
-enum { FLGF_CTX_LIST_PCT = 1, FLGF_CTX_TILE = 2 };
+enum { FLGF_CTX_LIST_PCT = 1, FLGF_CTX_TILE = 2, FLGF_CTX_FAIL_ALLOC = 3, FLGF_CTX_ORDER = 4 };
 int flgf_ctx_set_option(flgf_ctx* ctx, int key, int value);
 
 /* Message of the last failure on this context (never NULL; "" if none). */
@@ -134,6 +146,24 @@ int flgf_kernel_spectrum(flgf_ctx* ctx, int k, int d0, int d1, int d2, double* o
  * device buffers. */
 int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
                          const int32_t* coords, const double* h0, flgf_blockset** out);
+
+/* As flgf_blockset_create, for a solve sharded over several GPUs by target
+ * blocks (the multi-GPU form of Sec. 4's distribution of octants, with the
+ * source replicated instead of exchanged): want[i] (one byte per block, in the
+ * order of coords; NULL = every block) marks the blocks whose potential the
+ * caller needs.  The block set then evaluates the far and near fields
+ * (spectrum products, inverse FFTs, downward pass) only for those targets and
+ * their octree ancestors; every (problem, level) source must still be loaded
+ * in full.  The leaf-source fields that couple refinement levels (Sec. 3) are
+ * computed for all blocks, so the potential on a wanted block equals that of
+ * an unmasked solve; on other blocks it is unspecified.  Ranks that each
+ * create a block set wanting a disjoint part (e.g. contiguous Morton-order
+ * chunks) and gather their wanted blocks obtain the whole solution without
+ * exchanging data during the solve.  want is borrowed for the call.  The
+ * adjoint calls return FLGF_ESTATE on a block set that wants a subset. */
+int flgf_blockset_create_masked(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
+                                const int32_t* coords, const double* h0, const uint8_t* want,
+                                flgf_blockset** out);
 void flgf_blockset_destroy(flgf_blockset* bs);
 
 /* Total leaf cells (degrees of freedom of the composite mesh) over all problems. */
@@ -155,7 +185,10 @@ int flgf_load_source(flgf_blockset* bs, int problem, int level, const void* f, i
  * the FLGF of Sec. 2.1).  Enqueued on the context stream, no synchronisation. */
 int flgf_solve(flgf_blockset* bs);
 
-/* Copy u of (problem, level) into u ([nblk][N][N][N]); synchronises for HOST. */
+/* Copy u of (problem, level) into u ([nblk][N][N][N]).  Synchronises the
+ * context stream (both forms) and returns FLGF_EDEVICE if a kernel of the last
+ * solve raised the device error flag (a coarse-fine interpolation that met a
+ * missing halo block); the flag is cleared at the start of every solve. */
 int flgf_get_potential(flgf_blockset* bs, int problem, int level, void* u, int where);
 
 /* out = L_Q^{(h_l)} u on the blocks of (problem, level), using same-level face
@@ -176,7 +209,12 @@ int flgf_laplacian(flgf_blockset* bs, int problem, int level, const void* u, voi
  * potentials of the last flgf_solve stay valid.
  * Enqueued on the context stream; the source correction option applies.  The
  * first flgf_load_adjoint or flgf_solve_adjoint of a block set builds its
- * adjoint lists and allocates the adjoint buffers (FLGF_ENOMEM on failure). */
+ * adjoint lists and allocates the adjoint buffers (FLGF_ENOMEM on failure;
+ * a later call retries).  flgf_get_gradient synchronises like
+ * flgf_get_potential and reports the device error flag of the adjoint solve.
+ * The transposed coarse-fine interpolation adds the contributions of
+ * neighbouring fine blocks to shared coarse cells with atomic additions, so on
+ * refined meshes the gradient is reproducible to round-off, not bit for bit. */
 int flgf_load_adjoint(flgf_blockset* bs, int problem, int level, const void* g, int where);
 int flgf_solve_adjoint(flgf_blockset* bs);
 int flgf_get_gradient(flgf_blockset* bs, int problem, int level, void* out, int where);
@@ -185,7 +223,21 @@ int flgf_get_gradient(flgf_blockset* bs, int problem, int level, void* out, int 
 enum {
   FLGF_OPT_CORRECTION = 1,  /* 1 (default): source correction of Sec. 3 on; 0: off */
   FLGF_OPT_GRAPH = 2,       /* 1: capture the solve's launch sequence in a CUDA graph on first use */
-  FLGF_OPT_TIMING = 3       /* 1: record CUDA events between stages (see flgf_stage_times) */
+  FLGF_OPT_TIMING = 3,      /* 1: record CUDA events between stages (see flgf_stage_times) */
+  FLGF_OPT_COMPENSATED = 4, /* FP32 block sets: 1 runs the inverse FFTs of the octree levels above
+                               the finest and the downward-pass interpolation in compensated
+                               float-float arithmetic (about 48-bit significands on the FP32 pipes).
+                               The interpolation extrapolates those levels' fields to the outer
+                               faces of the child blocks, which amplifies FP32 rounding noise up to
+                               ~38x at block corners (n_I = 6); compensation keeps refined meshes
+                               within 1e-5 of the FP64 solve.  Default: 1 for block sets with a
+                               problem of two or more refinement levels, else 0.  No effect in
+                               FP64 contexts. */
+  FLGF_OPT_FAULT_HALO = 5   /* failure injection for tests (value 1): one coarse neighbour entry of
+                               the first coarse-fine interpolation list is marked absent, as if the
+                               mesh lacked that halo block; the following solve reads zero there and
+                               flgf_get_potential returns FLGF_EDEVICE.  Irreversible: the block
+                               set's results are wrong from then on. */
 };
 int flgf_set_option(flgf_blockset* bs, int key, int value);
 
@@ -221,7 +273,10 @@ int flgf_work_counts(const flgf_blockset* bs, int64_t* pairs, int64_t* fwd_ffts,
  * looks up that array's device address (cudaGetSymbolAddress); make that
  * first call outside any stream capture.  The call allocates nothing (no
  * cudaMalloc or cudaFree), enqueues its work on the context stream and does
- * not synchronise.  All calls on a device share the array, so calls whose
+ * not synchronise: its launch lists travel as the parameters of a small
+ * kernel that writes them into the array, so nothing is read from host memory
+ * after the call returns.  The library cannot check the sizes of f and u:
+ * they must hold nblk blocks.  All calls on a device share the array, so calls whose
  * GPU work may overlap (several contexts or streams on the same device) race;
  * serialise them.  Returns FLGF_EINVAL for more than 32 blocks or blocks
  * outside one aligned 4x4x4 box, FLGF_EMESH for duplicate blocks. */

@@ -20,6 +20,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "ffloat.cuh"
 #include "internal.h"
 
 namespace flgf {
@@ -27,18 +28,25 @@ namespace flgf {
 // e^{-2 pi i j / 32}, j = 0..31, filled once from the host.
 __constant__ double c_twd[32][2];
 __constant__ float c_twf[32][2];
+__constant__ float c_twff[32][4];  // (re hi, re lo, im hi, im lo)
 
 cudaError_t fft_init_constants() {
   double td[32][2];
-  float tf[32][2];
+  float tf[32][2], tff[32][4];
   for (int j = 0; j < 32; ++j) {
     const long double a = -2.0L * 3.141592653589793238462643383279502884L * j / 32.0L;
     td[j][0] = (double)cosl(a);
     td[j][1] = (double)sinl(a);
     tf[j][0] = (float)td[j][0];
     tf[j][1] = (float)td[j][1];
+    tff[j][0] = (float)cosl(a);
+    tff[j][1] = (float)(cosl(a) - (long double)tff[j][0]);
+    tff[j][2] = (float)sinl(a);
+    tff[j][3] = (float)(sinl(a) - (long double)tff[j][2]);
   }
   cudaError_t e = cudaMemcpyToSymbol(c_twd, td, sizeof(td));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_twff, tff, sizeof(tff));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_twf, tf, sizeof(tf));
 }
@@ -49,6 +57,8 @@ template <> __device__ __forceinline__ double tw_re<double>(int j) { return c_tw
 template <> __device__ __forceinline__ double tw_im<double>(int j) { return c_twd[j][1]; }
 template <> __device__ __forceinline__ float tw_re<float>(int j) { return c_twf[j][0]; }
 template <> __device__ __forceinline__ float tw_im<float>(int j) { return c_twf[j][1]; }
+template <> __device__ __forceinline__ ff tw_re<ff>(int j) { return ff(c_twff[j][0], c_twff[j][1]); }
+template <> __device__ __forceinline__ ff tw_im<ff>(int j) { return ff(c_twff[j][2], c_twff[j][3]); }
 
 // In-register radix-2 FFT of length L (<= 32), natural order in and out.
 // DIR = -1: forward (e^{-2 pi i jk/L}); DIR = +1: inverse without
@@ -150,13 +160,16 @@ __device__ __forceinline__ void fft_inv_pruned(const R* Xr, const R* Xi, R* xr, 
 // ---------------------------------------------------------------------------
 // Forward transform of source blocks.
 // ---------------------------------------------------------------------------
-template <typename R, int N>
+// R: storage type of the block values and spectra; C: arithmetic type of the
+// transform (R itself; the inverse also runs with the compensated ff on FP32
+// data).
+template <typename R, int N, typename C>
 __global__ void __launch_bounds__(N * N) fft_fwd_kernel(const R* __restrict__ nodes, const int* __restrict__ gids,
                                                         const int* __restrict__ sids, cplx<R>* __restrict__ spec,
                                                         int spec_blocks) {
   constexpr int P = 2 * N, NX = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* buf = reinterpret_cast<cplx<R>*>(smem_raw);  // [N z][P y][NX kx]
+  cplx<C>* buf = reinterpret_cast<cplx<C>*>(smem_raw);  // [N z][P y][NX kx]
   const int gid = gids[blockIdx.x], sid = sids[blockIdx.x];
   const R* in = nodes + (size_t)gid * N * N * N;
   const int tid = threadIdx.x;
@@ -168,7 +181,7 @@ __global__ void __launch_bounds__(N * N) fft_fwd_kernel(const R* __restrict__ no
   constexpr int V = 16 / (int)sizeof(R);  // values per 16-byte vector
   constexpr int RV = N / V;               // vectors per row
   constexpr int SU = RV + 1;              // staged row stride in vectors
-  static_assert(N * SU * 16 <= N * NX * (int)sizeof(cplx<R>), "staged plane fits the unused rows");
+  static_assert(N * SU * 16 <= N * NX * (int)sizeof(cplx<C>), "staged plane fits the unused rows");
   {
     const int4* src = reinterpret_cast<const int4*>(in);
     for (int i = tid; i < N * N * RV; i += blockDim.x) {
@@ -180,45 +193,45 @@ __global__ void __launch_bounds__(N * N) fft_fwd_kernel(const R* __restrict__ no
   // axis 2 (real input, N of 2N nonzero)
   for (int line = tid; line < N * N; line += blockDim.x) {
     const int z = line / N, y = line % N;
-    R xr[N], xi[N];
+    C xr[N], xi[N];
     const int4* stage = reinterpret_cast<const int4*>(buf + (z * P + N) * NX) + y * SU;
 #pragma unroll
     for (int u = 0; u < RV; ++u) {
       const int4 v = stage[u];
       const R* r = reinterpret_cast<const R*>(&v);
 #pragma unroll
-      for (int j = 0; j < V; ++j) { xr[u * V + j] = r[j]; xi[u * V + j] = R(0); }
+      for (int j = 0; j < V; ++j) { xr[u * V + j] = Arith<C>::from(r[j]); xi[u * V + j] = C(0.0f); }
     }
-    cplx<R>* row = buf + (z * P + y) * NX;
-    fft_fwd_pruned<P>(xr, xi, [&](int k, R re, R im) {
-      if (k <= N) row[k] = cplx<R>{re, im};
+    cplx<C>* row = buf + (z * P + y) * NX;
+    fft_fwd_pruned<P>(xr, xi, [&](int k, C re, C im) {
+      if (k <= N) row[k] = cplx<C>{re, im};
     });
   }
   __syncthreads();
   // axis 1 (N of 2N nonzero)
   for (int line = tid; line < N * NX; line += blockDim.x) {
     const int z = line / NX, kx = line % NX;
-    R xr[N], xi[N];
+    C xr[N], xi[N];
 #pragma unroll
     for (int y = 0; y < N; ++y) {
-      const cplx<R> v = buf[(z * P + y) * NX + kx];
+      const cplx<C> v = buf[(z * P + y) * NX + kx];
       xr[y] = v.re; xi[y] = v.im;
     }
-    fft_fwd_pruned<P>(xr, xi, [&](int k, R re, R im) { buf[(z * P + k) * NX + kx] = cplx<R>{re, im}; });
+    fft_fwd_pruned<P>(xr, xi, [&](int k, C re, C im) { buf[(z * P + k) * NX + kx] = cplx<C>{re, im}; });
   }
   __syncthreads();
   // axis 0 (N of 2N nonzero) -> HBM, chunked layout
   for (int line = tid; line < P * NX; line += blockDim.x) {
     const int ky = line / NX, kx = line % NX;
-    R xr[N], xi[N];
+    C xr[N], xi[N];
 #pragma unroll
     for (int z = 0; z < N; ++z) {
-      const cplx<R> v = buf[(z * P + ky) * NX + kx];
+      const cplx<C> v = buf[(z * P + ky) * NX + kx];
       xr[z] = v.re; xi[z] = v.im;
     }
-    fft_fwd_pruned<P>(xr, xi, [&](int k, R re, R im) {
+    fft_fwd_pruned<P>(xr, xi, [&](int k, C re, C im) {
       const int w = (k * P + ky) * NX + kx;
-      spec[spec_index<R>(w, sid, spec_blocks)] = cplx<R>{re, im};
+      spec[spec_index<R>(w, sid, spec_blocks)] = cplx<R>{Arith<C>::template to<R>(re), Arith<C>::template to<R>(im)};
     });
   }
 }
@@ -226,58 +239,58 @@ __global__ void __launch_bounds__(N * N) fft_fwd_kernel(const R* __restrict__ no
 // ---------------------------------------------------------------------------
 // Inverse transform of accumulated spectra; keeps the first N^3 outputs.
 // ---------------------------------------------------------------------------
-template <typename R, int N>
+template <typename R, int N, typename C>
 __global__ void __launch_bounds__(N * N) fft_inv_kernel(const cplx<R>* __restrict__ acc, int spec_blocks,
                                                         const int* __restrict__ sids, const int* __restrict__ gids,
                                                         const double* __restrict__ scales, R* __restrict__ out) {
   constexpr int P = 2 * N, NX = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* buf = reinterpret_cast<cplx<R>*>(smem_raw);  // [N z][P y][NX kx]
+  cplx<C>* buf = reinterpret_cast<cplx<C>*>(smem_raw);  // [N z][P y][NX kx]
   const int sid = sids[blockIdx.x], gid = gids[blockIdx.x];
   const int tid = threadIdx.x;
 
   // axis 0: 2N inputs from HBM, keep z < N
   for (int line = tid; line < P * NX; line += blockDim.x) {
     const int ky = line / NX, kx = line % NX;
-    R Xr[P], Xi[P];
+    C Xr[P], Xi[P];
 #pragma unroll
     for (int kz = 0; kz < P; ++kz) {
       const cplx<R> v = acc[spec_index<R>((kz * P + ky) * NX + kx, sid, spec_blocks)];
-      Xr[kz] = v.re; Xi[kz] = v.im;
+      Xr[kz] = Arith<C>::from(v.re); Xi[kz] = Arith<C>::from(v.im);
     }
-    R xr[N], xi[N];
+    C xr[N], xi[N];
     fft_inv_pruned<P>(Xr, Xi, xr, xi);
 #pragma unroll
-    for (int z = 0; z < N; ++z) buf[(z * P + ky) * NX + kx] = cplx<R>{xr[z], xi[z]};
+    for (int z = 0; z < N; ++z) buf[(z * P + ky) * NX + kx] = cplx<C>{xr[z], xi[z]};
   }
   __syncthreads();
   // axis 1: keep y < N
   for (int line = tid; line < N * NX; line += blockDim.x) {
     const int z = line / NX, kx = line % NX;
-    R Xr[P], Xi[P];
+    C Xr[P], Xi[P];
 #pragma unroll
     for (int ky = 0; ky < P; ++ky) {
-      const cplx<R> v = buf[(z * P + ky) * NX + kx];
+      const cplx<C> v = buf[(z * P + ky) * NX + kx];
       Xr[ky] = v.re; Xi[ky] = v.im;
     }
-    R xr[N], xi[N];
+    C xr[N], xi[N];
     fft_inv_pruned<P>(Xr, Xi, xr, xi);
 #pragma unroll
-    for (int y = 0; y < N; ++y) buf[(z * P + y) * NX + kx] = cplx<R>{xr[y], xi[y]};
+    for (int y = 0; y < N; ++y) buf[(z * P + y) * NX + kx] = cplx<C>{xr[y], xi[y]};
   }
   __syncthreads();
   // axis 2: Hermitian half -> real, keep x < N
-  const R scale = (R)(scales[blockIdx.x] / (double)(P * P * P));
+  const C scale = Arith<C>::from_d(scales[blockIdx.x] / (double)(P * P * P));
   R* o = out + (size_t)gid * N * N * N;
   for (int line = tid; line < N * N; line += blockDim.x) {
     const int z = line / N, y = line % N;
-    const cplx<R>* row = buf + (z * P + y) * NX;
-    R Xr[P], Xi[P];
+    const cplx<C>* row = buf + (z * P + y) * NX;
+    C Xr[P], Xi[P];
 #pragma unroll
-    for (int k = 0; k <= N; ++k) { const cplx<R> v = row[k]; Xr[k] = v.re; Xi[k] = v.im; }
+    for (int k = 0; k <= N; ++k) { const cplx<C> v = row[k]; Xr[k] = v.re; Xi[k] = v.im; }
 #pragma unroll
     for (int k = N + 1; k < P; ++k) { Xr[k] = Xr[P - k]; Xi[k] = -Xi[P - k]; }
-    R xr[N], xi[N];
+    C xr[N], xi[N];
     fft_inv_pruned<P>(Xr, Xi, xr, xi);
     constexpr int V = 16 / (int)sizeof(R);
     int4* orow = reinterpret_cast<int4*>(o + (z * N + y) * N);
@@ -286,7 +299,7 @@ __global__ void __launch_bounds__(N * N) fft_inv_kernel(const cplx<R>* __restric
       int4 v;
       R* r = reinterpret_cast<R*>(&v);
 #pragma unroll
-      for (int j = 0; j < V; ++j) r[j] = scale * xr[u * V + j];
+      for (int j = 0; j < V; ++j) r[j] = Arith<C>::template to<R>(scale * xr[u * V + j]);
       orow[u] = v;
     }
   }
@@ -364,19 +377,34 @@ static cudaError_t set_smem(Kern k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename R>
-cudaError_t launch_fft_forward(int N, const R* nodes, const int* gids, const int* sids, int count, void* spec,
-                               int spec_blocks, cudaStream_t s) {
-  if (count <= 0) return cudaSuccess;
-  cplx<R>* sp = reinterpret_cast<cplx<R>*>(spec);
+template <typename R, typename C>
+static cudaError_t launch_fwd(int N, const R* nodes, const int* gids, const int* sids, int count, cplx<R>* sp,
+                              int spec_blocks, cudaStream_t s) {
   if (N == 16) {
-    const size_t sm = sizeof(cplx<R>) * 16 * 32 * 17;
-    cudaError_t e = set_smem(fft_fwd_kernel<R, 16>, sm);
+    const size_t sm = sizeof(cplx<C>) * 16 * 32 * 17;
+    cudaError_t e = set_smem(fft_fwd_kernel<R, 16, C>, sm);
     if (e != cudaSuccess) return e;
-    fft_fwd_kernel<R, 16><<<count, 256, sm, s>>>(nodes, gids, sids, sp, spec_blocks);
+    fft_fwd_kernel<R, 16, C><<<count, 256, sm, s>>>(nodes, gids, sids, sp, spec_blocks);
   } else if (N == 8) {
-    const size_t sm = sizeof(cplx<R>) * 8 * 16 * 9;
-    fft_fwd_kernel<R, 8><<<count, 64, sm, s>>>(nodes, gids, sids, sp, spec_blocks);
+    const size_t sm = sizeof(cplx<C>) * 8 * 16 * 9;
+    fft_fwd_kernel<R, 8, C><<<count, 64, sm, s>>>(nodes, gids, sids, sp, spec_blocks);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R, typename C>
+static cudaError_t launch_inv(int N, const cplx<R>* ac, int spec_blocks, const int* sids, const int* gids,
+                              const double* scales, int count, R* out, cudaStream_t s) {
+  if (N == 16) {
+    const size_t sm = sizeof(cplx<C>) * 16 * 32 * 17;
+    cudaError_t e = set_smem(fft_inv_kernel<R, 16, C>, sm);
+    if (e != cudaSuccess) return e;
+    fft_inv_kernel<R, 16, C><<<count, 256, sm, s>>>(ac, spec_blocks, sids, gids, scales, out);
+  } else if (N == 8) {
+    const size_t sm = sizeof(cplx<C>) * 8 * 16 * 9;
+    fft_inv_kernel<R, 8, C><<<count, 64, sm, s>>>(ac, spec_blocks, sids, gids, scales, out);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -384,22 +412,21 @@ cudaError_t launch_fft_forward(int N, const R* nodes, const int* gids, const int
 }
 
 template <typename R>
+cudaError_t launch_fft_forward(int N, const R* nodes, const int* gids, const int* sids, int count, void* spec,
+                               int spec_blocks, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  return launch_fwd<R, R>(N, nodes, gids, sids, count, reinterpret_cast<cplx<R>*>(spec), spec_blocks, s);
+}
+
+template <typename R>
 cudaError_t launch_fft_inverse(int N, const void* acc, int spec_blocks, const int* sids, const int* gids,
-                               const double* scales, int count, R* out, cudaStream_t s) {
+                               const double* scales, int count, R* out, cudaStream_t s, bool compensated) {
   if (count <= 0) return cudaSuccess;
   const cplx<R>* ac = reinterpret_cast<const cplx<R>*>(acc);
-  if (N == 16) {
-    const size_t sm = sizeof(cplx<R>) * 16 * 32 * 17;
-    cudaError_t e = set_smem(fft_inv_kernel<R, 16>, sm);
-    if (e != cudaSuccess) return e;
-    fft_inv_kernel<R, 16><<<count, 256, sm, s>>>(ac, spec_blocks, sids, gids, scales, out);
-  } else if (N == 8) {
-    const size_t sm = sizeof(cplx<R>) * 8 * 16 * 9;
-    fft_inv_kernel<R, 8><<<count, 64, sm, s>>>(ac, spec_blocks, sids, gids, scales, out);
-  } else {
-    return cudaErrorInvalidValue;
+  if constexpr (sizeof(R) == 4) {
+    if (compensated) return launch_inv<R, ff>(N, ac, spec_blocks, sids, gids, scales, count, out, s);
   }
-  return cudaGetLastError();
+  return launch_inv<R, R>(N, ac, spec_blocks, sids, gids, scales, count, out, s);
 }
 
 template <typename R>
@@ -427,9 +454,12 @@ cudaError_t launch_kernel_spectra(int N, const double* karr, void* kspec_level, 
 }
 
 template cudaError_t launch_fft_forward<float>(int, const float*, const int*, const int*, int, void*, int, cudaStream_t);
-template cudaError_t launch_fft_forward<double>(int, const double*, const int*, const int*, int, void*, int, cudaStream_t);
-template cudaError_t launch_fft_inverse<float>(int, const void*, int, const int*, const int*, const double*, int, float*, cudaStream_t);
-template cudaError_t launch_fft_inverse<double>(int, const void*, int, const int*, const int*, const double*, int, double*, cudaStream_t);
+template cudaError_t launch_fft_forward<double>(int, const double*, const int*, const int*, int, void*, int,
+                                                cudaStream_t);
+template cudaError_t launch_fft_inverse<float>(int, const void*, int, const int*, const int*, const double*, int, float*,
+                                               cudaStream_t, bool);
+template cudaError_t launch_fft_inverse<double>(int, const void*, int, const int*, const int*, const double*, int,
+                                                double*, cudaStream_t, bool);
 template cudaError_t launch_kernel_spectra<float>(int, const double*, void*, double*, int, cudaStream_t);
 template cudaError_t launch_kernel_spectra<double>(int, const double*, void*, double*, int, cudaStream_t);
 

@@ -23,6 +23,10 @@ struct flgf_ctx {
   // plan options for block sets created afterwards (flgf_ctx_set_option)
   int list_pct = 30;             // pair-list MAC below this useful fraction of the dense kernel's work
   int tile[3] = {4, 4, 8};       // dense MAC tile in parents
+  bool order_by_list = false;    // dense MAC groups: parents ordered by neighbour set (FLGF_CTX_ORDER)
+  // failure injection (FLGF_CTX_FAIL_ALLOC): the fail_alloc_at-th block-set
+  // device allocation from the arming on reports out-of-memory instead of allocating
+  int fail_alloc_at = 0, alloc_count = 0;
   cudaStream_t stream = nullptr;
   std::string err;
   double* d_table = nullptr;
@@ -39,6 +43,17 @@ using I3 = std::array<int, 3>;
 int fail(flgf_ctx* c, int code, const std::string& m) {
   if (c) c->err = m;
   return code;
+}
+
+// Device allocation of block-set buffers (at least 256 bytes), with the
+// failure-injection hook of FLGF_CTX_FAIL_ALLOC.
+cudaError_t dev_alloc(flgf_ctx* ctx, void** p, size_t bytes) {
+  if (ctx->fail_alloc_at > 0 && ++ctx->alloc_count == ctx->fail_alloc_at) {
+    ctx->fail_alloc_at = 0;
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, std::max<size_t>(bytes, 256));
 }
 
 #define CK(call)                                                                                     \
@@ -117,6 +132,7 @@ struct LevelInfo {
   std::vector<I3> c;
   std::vector<uint8_t> leaf;
   std::vector<uint8_t> ext;  // non-leaf block or a neighbour of one: where W^l is needed
+  std::vector<uint8_t> want; // the caller wants u here (flgf_blockset_create_masked; all by default)
   std::unordered_map<uint64_t, int> idx;
   int fw0 = 0;      // first block in fuser / fwork
   int ugid0 = 0;    // first global id of u^l (instance 0, octree level 0)
@@ -139,7 +155,7 @@ struct PhaseOff {  // arena offsets and counts of one phase's launch lists
   int n_groups_dense = 0, n_work = 0, max_units = 0;
   size_t hgroups = 0, work = 0, src_ids = 0, tgt_ids = 0, par_tab = 0;
   int n_groups = 0, max_group_src = 0; size_t groups = 0, l_tgt = 0, l_len = 0, l_ent = 0, l_src = 0;
-  int n_inv = 0; size_t inv_sid = 0, inv_gid = 0, inv_scale = 0;
+  int n_inv = 0, n_inv0 = 0; size_t inv_sid = 0, inv_gid = 0, inv_scale = 0;  // finest octree level first (n_inv0)
   std::vector<int> n_itp; std::vector<size_t> itp_ch, itp_par, itp_cpos;
   int n_sel = 0; size_t sel_src = 0, sel_dst = 0;
   int n_selw = 0; size_t selw_src = 0, selw_dst = 0;
@@ -199,6 +215,8 @@ struct flgf_blockset {
   bool load_pending = false;
   bool correction = true, solved = false;
   bool use_graph = false, timing = false;
+  bool compensated = false;  // FLGF_OPT_COMPENSATED (FP32 block sets)
+  bool masked = false;       // created with a target mask (flgf_blockset_create_masked)
   cudaGraphExec_t gexec = nullptr;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;  // (stage, (start, end))
   size_t ev_used = 0;
@@ -426,8 +444,9 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
   for (const Inst* in : insts) maxtop = std::max(maxtop, in->top);
   std::vector<std::vector<int>> ant_par(maxtop + 1), ant_ch(maxtop + 1);
   std::vector<std::vector<int>> itp_ch(maxtop + 1), itp_par(maxtop + 1), itp_cpos(maxtop + 1);
-  std::vector<int> fwd_gid, fwd_sid, inv_sid, inv_gid;
-  std::vector<double> inv_scale;
+  // inverse FFT list: finest octree level, then the coarser ones (their own launch)
+  std::vector<int> fwd_gid, fwd_sid, inv_sid, inv_gid, inv_sid_c, inv_gid_c;
+  std::vector<double> inv_scale, inv_scale_c;
   // parents with targets of dense tiles per octree level, in tile order
   std::vector<std::vector<ParentRec>> dpool;
   std::vector<ListGroup> groups;
@@ -612,9 +631,9 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
           fwd_sid.push_back(gid - ph.gid_begin);
         }
         if (in.need_tgt[k][i]) {
-          inv_sid.push_back(gid - ph.gid_begin);
-          inv_gid.push_back(gid);
-          inv_scale.push_back(in.h * in.h);
+          (k == 0 ? inv_sid : inv_sid_c).push_back(gid - ph.gid_begin);
+          (k == 0 ? inv_gid : inv_gid_c).push_back(gid);
+          (k == 0 ? inv_scale : inv_scale_c).push_back(in.h * in.h);
           if ((int)k < in.top) {
             const I3& c = in.lv[k][i];
             const int pi = in.idx[k + 1].at(key3(c[0] >> 1, c[1] >> 1, c[2] >> 1));
@@ -627,6 +646,10 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
       jobs.push_back(TileJob{&in, (int)k});
     }
   }
+  const int n_inv0 = (int)inv_gid.size();
+  inv_gid.insert(inv_gid.end(), inv_gid_c.begin(), inv_gid_c.end());
+  inv_sid.insert(inv_sid.end(), inv_sid_c.begin(), inv_sid_c.end());
+  inv_scale.insert(inv_scale.end(), inv_scale_c.begin(), inv_scale_c.end());
   // run the tile jobs on the host's cores; the results are merged in job order,
   // so the launch lists do not depend on the number of threads
   {
@@ -661,7 +684,7 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
   // dense MAC: parent groups of every octree level
   HadLists hl;
   for (int k = 0; k < (int)dpool.size(); ++k)
-    pack_parent_groups(k, dpool[k], nchunk, had_kernel_units(ctx->prec == FLGF_FP64), hl);
+    pack_parent_groups(k, dpool[k], nchunk, had_kernel_units(ctx->prec == FLGF_FP64), hl, ctx->order_by_list);
   // pair-list groups: consecutive pool targets (spatially close, so their
   // source sets overlap) up to kListTargets targets or kListMaxSrc sources
   for (int k = 0; k < (int)lpool.size(); ++k) {
@@ -755,6 +778,7 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
   ph.l_ent = ar.add(l_ent);
   ph.l_src = ar.add(l_src);
   ph.n_inv = (int)inv_gid.size();
+  ph.n_inv0 = n_inv0;
   ph.inv_sid = ar.add(inv_sid);
   ph.inv_gid = ar.add(inv_gid);
   ph.inv_scale = ar.add(inv_scale);
@@ -764,7 +788,7 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
 // CUDA call), so the planning can be exercised without a GPU.  On failure the
 // caller destroys bs.
 static int plan_blockset(flgf_ctx* ctx, flgf_blockset* bs, int n_problems, const int* n_levels, const int* nblk,
-                         const int32_t* coords, const double* h0) {
+                         const int32_t* coords, const double* h0, const uint8_t* want = nullptr) {
   const int N = ctx->N;
   const size_t N3 = (size_t)N * N * N;
   auto bail = [&](int code, const std::string& m) { return fail(ctx, code, m); };
@@ -784,7 +808,9 @@ static int plan_blockset(flgf_ctx* ctx, flgf_blockset* bs, int n_problems, const
       const int nb = nblk[q];
       if (nb < 1) return bail(FLGF_EINVAL, "every level needs at least one block");
       L.c.resize(nb);
+      L.want.assign(nb, 1);
       for (int b = 0; b < nb; ++b, ++ci) {
+        if (want) L.want[b] = want[ci] != 0;
         for (int a = 0; a < 3; ++a) {
           const int v = coords[3 * ci + a];
           if (v < -(1 << 19) || v >= (1 << 19)) return bail(FLGF_EINVAL, "block coordinate out of range");
@@ -870,7 +896,17 @@ static int plan_blockset(flgf_ctx* ctx, flgf_blockset* bs, int n_problems, const
           in.gid0[k] = bs->G;
           bs->G += (int)in.lv[k].size();
           in.is_src[k].assign(in.lv[k].size(), 1);
-          in.need_tgt[k].assign(in.lv[k].size(), variant == 0 ? 1 : 0);
+          in.need_tgt[k].assign(in.lv[k].size(), 0);
+        }
+        if (variant == 0) {  // targets: the wanted blocks and their octree ancestors
+          for (size_t b = 0; b < L.c.size(); ++b) {
+            if (!L.want[b]) continue;
+            I3 c = L.c[b];
+            for (size_t k = 0; k < in.lv.size(); ++k) {
+              in.need_tgt[k][in.idx[k][key3(c)]] = 1;
+              c = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
+            }
+          }
         }
         if (variant == 1) {
           for (size_t b = 0; b < L.c.size(); ++b) {
@@ -1007,8 +1043,8 @@ static int plan_blockset(flgf_ctx* ctx, flgf_blockset* bs, int n_problems, const
   return FLGF_OK;
 }
 
-extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
-                                    const int32_t* coords, const double* h0, flgf_blockset** out) {
+static int blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
+                           const int32_t* coords, const double* h0, const uint8_t* want, flgf_blockset** out) {
   if (!ctx || !out || n_problems < 1 || !n_levels || !nblk || !coords || !h0)
     return fail(ctx, FLGF_EINVAL, "blockset_create: bad arguments");
   *out = nullptr;
@@ -1019,18 +1055,22 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
     flgf_blockset_destroy(bs);
     return fail(ctx, code, m);
   };
-  const int rc = plan_blockset(ctx, bs, n_problems, n_levels, nblk, coords, h0);
+  const int rc = plan_blockset(ctx, bs, n_problems, n_levels, nblk, coords, h0, want);
   if (rc != FLGF_OK) {
     flgf_blockset_destroy(bs);
     return rc;
   }
+  bs->compensated = ctx->prec == FLGF_FP32 && bs->Lmax >= 2;
+  for (const auto& P : bs->prob)
+    for (const auto& L : P.lev)
+      bs->masked |= std::any_of(L.want.begin(), L.want.end(), [](uint8_t v) { return v == 0; });
   const int N = ctx->N;
   const size_t N3 = (size_t)N * N * N;
   Arena& ar = bs->ar;
   // ---- device memory ---------------------------------------------------------
   const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4;
   const size_t NW = (size_t)nfreq(N);
-  auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 256)); };
+  auto alloc = [&](void** p, size_t bytes) { return dev_alloc(ctx, p, bytes); };
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = alloc((void**)&ar.dev, ar.host.size());
   if (e == cudaSuccess) e = cudaMemcpy(ar.dev, ar.host.data(), ar.host.size(), cudaMemcpyHostToDevice);
@@ -1059,12 +1099,25 @@ extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_
   return FLGF_OK;
 }
 
+extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
+                                    const int32_t* coords, const double* h0, flgf_blockset** out) {
+  return blockset_create(ctx, n_problems, n_levels, nblk, coords, h0, nullptr, out);
+}
+
+extern "C" int flgf_blockset_create_masked(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
+                                           const int32_t* coords, const double* h0, const uint8_t* want,
+                                           flgf_blockset** out) {
+  return blockset_create(ctx, n_problems, n_levels, nblk, coords, h0, want, out);
+}
+
 // Adjoint plan, built on first use: the transposed leaf-only instances, their
 // FMM lists and the transposed coupling lists (in their own arena), and the
 // adjoint buffers.  Forward-only users pay neither its host time nor its
 // device memory.
 static int build_adjoint(flgf_blockset* bs) {
   flgf_ctx* ctx = bs->ctx;
+  // the adjoint reuses the forward lists, which a target mask has pruned
+  if (bs->masked) return fail(ctx, FLGF_ESTATE, "the adjoint needs a block set without a target mask");
   const size_t N3 = (size_t)ctx->N * ctx->N * ctx->N;
   // start from nothing, so a call after a failed one (out of memory) rebuilds cleanly
   for (void** p : {&bs->gseed, &bs->gW, &bs->gf, &bs->gtmp, &bs->aunodes}) {
@@ -1168,7 +1221,7 @@ static int build_adjoint(flgf_blockset* bs) {
     ao.cf1_ih2 = aar.add(c1h);
   }
   const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4;
-  auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 256)); };
+  auto alloc = [&](void** p, size_t bytes) { return dev_alloc(ctx, p, bytes); };
   cudaError_t e = alloc((void**)&aar.dev, aar.host.size());
   if (e == cudaSuccess) e = cudaMemcpy(aar.dev, aar.host.data(), aar.host.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = alloc(&bs->gseed, rs * N3 * bs->B);
@@ -1294,6 +1347,13 @@ cudaError_t enqueue_fmm(flgf_blockset* bs, const Arena& ar, const PhaseOff& ph, 
       KRUN(ph.n_ant[k], launch_anterp<R>(N, c->nI, c->d_J1, ar.at<int>(ph.ant_par[k]), ar.at<int>(ph.ant_ch[k]),
                                          ph.n_ant[k], nodes, s));
   }
+  // The fields of the octree levels above the finest are extrapolated to the
+  // outer faces of the child blocks by the downward pass, whose Lagrange rows
+  // there amplify white rounding noise ~38x at a block corner (n_I = 6).  With
+  // FLGF_OPT_COMPENSATED an FP32 block set therefore transforms those levels
+  // back (inverse FFT) and interpolates in float-float arithmetic; the finest
+  // level's inverse FFTs, which nothing amplifies, stay plain FP32.
+  const bool comp = bs->compensated;
   {
     StageScope sc(bs, 2);
     KRUN(ph.n_fwd, launch_fft_forward<R>(N, nodes, ar.at<int>(ph.fwd_gid), ar.at<int>(ph.fwd_sid), ph.n_fwd, bs->spec,
@@ -1303,7 +1363,7 @@ cudaError_t enqueue_fmm(flgf_blockset* bs, const Arena& ar, const PhaseOff& ph, 
     StageScope sc(bs, 3);
     KRUN(ph.n_work, launch_hadamard<R>(N, ar.at<HadGroup>(ph.hgroups), ar.at<HadWork>(ph.work), ph.n_work,
                                        ph.max_units, ar.at<int>(ph.src_ids), ar.at<int>(ph.tgt_ids),
-                                       ar.at<int16_t>(ph.par_tab), bs->spec, bs->acc, ph.nblocks, c->d_kspec,
+                                       ar.at<uint16_t>(ph.par_tab), bs->spec, bs->acc, ph.nblocks, c->d_kspec,
                                        c->kstride, s));
     KRUN(ph.n_groups, launch_hadamard_list<R>(N, ar.at<ListGroup>(ph.groups), ph.n_groups, ph.max_group_src,
                                               ar.at<int>(ph.l_tgt), ar.at<int>(ph.l_len), ar.at<int>(ph.l_ent),
@@ -1312,14 +1372,18 @@ cudaError_t enqueue_fmm(flgf_blockset* bs, const Arena& ar, const PhaseOff& ph, 
   }
   {
     StageScope sc(bs, 4);
-    KRUN(ph.n_inv, launch_fft_inverse<R>(N, bs->acc, ph.nblocks, ar.at<int>(ph.inv_sid), ar.at<int>(ph.inv_gid),
-                                         ar.at<double>(ph.inv_scale), ph.n_inv, unodes, s));
+    KRUN(ph.n_inv0, launch_fft_inverse<R>(N, bs->acc, ph.nblocks, ar.at<int>(ph.inv_sid), ar.at<int>(ph.inv_gid),
+                                          ar.at<double>(ph.inv_scale), ph.n_inv0, unodes, s, false));
+    const int nc = ph.n_inv - ph.n_inv0;
+    KRUN(nc, launch_fft_inverse<R>(N, bs->acc, ph.nblocks, ar.at<int>(ph.inv_sid) + ph.n_inv0,
+                                   ar.at<int>(ph.inv_gid) + ph.n_inv0, ar.at<double>(ph.inv_scale) + ph.n_inv0, nc,
+                                   unodes, s, comp));
   }
   {
     StageScope sc(bs, 5);
     for (int k = maxtop - 1; k >= 0; --k)
       KRUN(ph.n_itp[k], launch_interp_add<R>(N, c->nI, c->d_J1, ar.at<int>(ph.itp_ch[k]), ar.at<int>(ph.itp_par[k]),
-                                             ar.at<int>(ph.itp_cpos[k]), ph.n_itp[k], unodes, s));
+                                             ar.at<int>(ph.itp_cpos[k]), ph.n_itp[k], unodes, s, comp));
   }
 #undef KRUN
   return cudaSuccess;
@@ -1351,6 +1415,7 @@ cudaError_t enqueue_adjoint(flgf_blockset* bs) {
     if ((e = (x)) != cudaSuccess) return e;     \
   } while (0)
   bs->launches = 0;
+  RUN(cudaMemsetAsync(bs->d_err, 0, sizeof(int), s));
   RUN(cudaMemsetAsync(gW, 0, sizeof(R) * N3 * bs->B, s));
   RUN(cudaMemsetAsync(gf, 0, sizeof(R) * N3 * bs->B, s));
   for (int l = bs->Lmax - 1; l >= 0; --l) {
@@ -1406,6 +1471,7 @@ cudaError_t enqueue_solve(flgf_blockset* bs) {
     if ((e = (x)) != cudaSuccess) return e;     \
   } while (0)
   bs->launches = 0;
+  RUN(cudaMemsetAsync(bs->d_err, 0, sizeof(int), s));
   RUN(cudaMemcpyAsync(fwork, bs->fuser, sizeof(R) * N3 * bs->B, cudaMemcpyDeviceToDevice, s));
   RUN(cudaEventRecordWithFlags(bs->ev_fuser_free, s, bs->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   {
@@ -1469,6 +1535,15 @@ extern "C" int flgf_ctx_set_option(flgf_ctx* ctx, int key, int value) {
       if (value < 0 || value > 100) return fail(ctx, FLGF_EINVAL, "list percentage must be 0..100");
       ctx->list_pct = value;
       return FLGF_OK;
+    case FLGF_CTX_ORDER:
+      if (value != 0 && value != 1) return fail(ctx, FLGF_EINVAL, "FLGF_CTX_ORDER takes 0 or 1");
+      ctx->order_by_list = value == 1;
+      return FLGF_OK;
+    case FLGF_CTX_FAIL_ALLOC:
+      if (value < 0) return fail(ctx, FLGF_EINVAL, "allocation failure index must be >= 0");
+      ctx->fail_alloc_at = value;
+      ctx->alloc_count = 0;
+      return FLGF_OK;
     case FLGF_CTX_TILE: {
       const int t[3] = {value & 255, (value >> 8) & 255, (value >> 16) & 255};
       for (int a = 0; a < 3; ++a)
@@ -1497,6 +1572,32 @@ extern "C" int flgf_set_option(flgf_blockset* bs, int key, int value) {
       break;
     case FLGF_OPT_TIMING:
       bs->timing = value != 0;
+      break;
+    case FLGF_OPT_FAULT_HALO: {
+      // failure injection: mark one coarse neighbour of the first coarse-fine
+      // accumulation list absent, in the host copy and on the device, as if
+      // the mesh lacked that halo block (the kernel then reads zero there and
+      // raises the device error flag)
+      if (value != 1) return fail(ctx, FLGF_EINVAL, "FLGF_OPT_FAULT_HALO takes 1");
+      for (const PhaseOff& ph : bs->ph) {
+        if (ph.n_acc == 0) continue;
+        int* h = reinterpret_cast<int*>(bs->ar.host.data() + ph.acc_nbr);
+        for (int i = 13; i < 27 * ph.n_acc; i += 27) {  // the parent itself: read for every child position
+          if (h[i] < 0) continue;
+          h[i] = -1;
+          CK(cudaMemcpy(bs->ar.dev + ph.acc_nbr + sizeof(int) * i, &h[i], sizeof(int), cudaMemcpyHostToDevice));
+          if (bs->gexec) {
+            cudaGraphExecDestroy(bs->gexec);
+            bs->gexec = nullptr;
+          }
+          return FLGF_OK;
+        }
+      }
+      return fail(ctx, FLGF_EINVAL, "FLGF_OPT_FAULT_HALO: the block set has no coarse-fine interpolation");
+    }
+    case FLGF_OPT_COMPENSATED:
+      if (value != 0 && value != 1) return fail(ctx, FLGF_EINVAL, "FLGF_OPT_COMPENSATED takes 0 or 1");
+      bs->compensated = value == 1 && ctx->prec == FLGF_FP32;
       break;
     default:
       return fail(ctx, FLGF_EINVAL, "unknown option");
@@ -1558,6 +1659,19 @@ extern "C" int flgf_stage_times(flgf_blockset* bs, double* ms, int n_stages, int
   return FLGF_OK;
 }
 
+namespace {
+// Waits for the context stream and reports the device error flag that the
+// kernels of the last solve (forward or adjoint) raise on a missing halo block.
+int check_device_flag(flgf_blockset* bs, const char* what) {
+  flgf_ctx* ctx = bs->ctx;
+  CK(cudaStreamSynchronize(ctx->stream));
+  int herr = 0;
+  CK(cudaMemcpy(&herr, bs->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) return fail(ctx, FLGF_EDEVICE, std::string(what) + ": a coarse-fine interpolation met a missing halo block");
+  return FLGF_OK;
+}
+}  // namespace
+
 extern "C" int flgf_load_adjoint(flgf_blockset* bs, int problem, int level, const void* g, int where) {
   if (!bs || !g || (where != FLGF_HOST && where != FLGF_DEVICE)) return FLGF_EINVAL;
   flgf_ctx* ctx = bs->ctx;
@@ -1597,8 +1711,7 @@ extern "C" int flgf_get_gradient(flgf_blockset* bs, int problem, int level, void
   const LevelInfo& L = bs->prob[problem].lev[level];
   const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4, N3 = (size_t)ctx->N * ctx->N * ctx->N;
   CK(cudaMemcpyAsync(out, (char*)bs->gf + rs * N3 * L.fw0, rs * N3 * L.c.size(), kind(where, false), ctx->stream));
-  if (where == FLGF_HOST) CK(cudaStreamSynchronize(ctx->stream));
-  return FLGF_OK;
+  return check_device_flag(bs, "get_gradient");
 }
 
 extern "C" int flgf_get_potential(flgf_blockset* bs, int problem, int level, void* u, int where) {
@@ -1609,13 +1722,7 @@ extern "C" int flgf_get_potential(flgf_blockset* bs, int problem, int level, voi
   const LevelInfo& L = bs->prob[problem].lev[level];
   const size_t rs = ctx->prec == FLGF_FP64 ? 8 : 4, N3 = (size_t)ctx->N * ctx->N * ctx->N;
   CK(cudaMemcpyAsync(u, (char*)bs->unodes + rs * N3 * L.ugid0, rs * N3 * L.c.size(), kind(where, false), ctx->stream));
-  if (where == FLGF_HOST) {
-    CK(cudaStreamSynchronize(ctx->stream));
-    int herr = 0;
-    CK(cudaMemcpy(&herr, bs->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (herr) return fail(ctx, FLGF_EDEVICE, "a coarse-fine interpolation met a missing halo block");
-  }
-  return FLGF_OK;
+  return check_device_flag(bs, "get_potential");
 }
 
 extern "C" int flgf_laplacian(flgf_blockset* bs, int problem, int level, const void* u, void* out, int where) {

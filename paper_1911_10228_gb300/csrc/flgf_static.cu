@@ -58,12 +58,43 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-template <typename T>
-size_t put(std::vector<unsigned char>& buf, const std::vector<T>& v) {
-  const size_t off = (buf.size() + 255) & ~(size_t)255;
-  buf.resize(off + v.size() * sizeof(T));
-  if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
-  return off;
+// Launch lists of one call, passed to the list-writing kernel by value (the
+// kernel's parameters are copied at launch, so nothing is read from host
+// memory afterwards).  At most 8 parents with targets and 8 neighbour cells
+// with sources: the blocks lie in one aligned 4x4x4 box.
+struct StaticLists {
+  HadGroup group;
+  int nchunk, nblk;
+  double h2;
+  int src[8 * 8];
+  int tgt[8 * 8];
+  uint16_t par[27 * 8];
+};
+
+// Offsets of the lists in the scratch array (256-byte aligned).
+constexpr size_t kOffGroup = 0;
+constexpr size_t kOffIds = 256;
+constexpr size_t kOffScale = kOffIds + 256;
+constexpr size_t kOffSrc = kOffScale + 256;
+constexpr size_t kOffTgt = kOffSrc + 256;
+constexpr size_t kOffPar = kOffTgt + 256;
+constexpr size_t kOffWork = kOffPar + 512;
+
+__global__ void static_lists_kernel(const StaticLists L, unsigned char* __restrict__ dl) {
+  const int t = threadIdx.x;
+  if (t == 0) *reinterpret_cast<HadGroup*>(dl + kOffGroup) = L.group;
+  if (t < L.nblk) {
+    reinterpret_cast<int*>(dl + kOffIds)[t] = t;
+    reinterpret_cast<double*>(dl + kOffScale)[t] = L.h2;
+  }
+  if (t < 8 * L.group.ncell) reinterpret_cast<int*>(dl + kOffSrc)[t] = L.src[t];
+  if (t < 8 * L.group.nact) reinterpret_cast<int*>(dl + kOffTgt)[t] = L.tgt[t];
+  if (t < 27 * L.group.nact) reinterpret_cast<uint16_t*>(dl + kOffPar)[t] = L.par[t];
+  // work items: (group 0, first chunk, chunks), cpc chunks each
+  HadWork* w = reinterpret_cast<HadWork*>(dl + kOffWork);
+  const int cpc = L.group.cpc;
+  for (int i = t; i * cpc < L.nchunk; i += blockDim.x)
+    w[i] = HadWork{0, i * cpc, min(cpc, L.nchunk - i * cpc)};
 }
 
 }  // namespace
@@ -126,14 +157,19 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
   const int nchunk = cv.fp64 ? nchunks<double>(N) : nchunks<float>(N);
   HadLists hl;
   pack_parent_groups(0, recs, nchunk, had_kernel_units(cv.fp64), hl);
-  std::vector<int> ids(nblk);
-  for (int b = 0; b < nblk; ++b) ids[b] = b;
-  std::vector<double> scales(nblk, h * h);
-  std::vector<unsigned char> lists;
-  const size_t o_groups = put(lists, hl.groups), o_work = put(lists, hl.work), o_src = put(lists, hl.src_ids),
-               o_tgt = put(lists, hl.tgt_ids), o_par = put(lists, hl.par_tab);
-  const size_t o_ids = put(lists, ids), o_scale = put(lists, scales);
-  if (lists.size() > kListBytes) return bad(FLGF_EINVAL, "convolve_static: launch lists exceed the scratch");
+  // one group of at most 8 parents and 8 cells (the parents lie in a 2x2x2 box)
+  if (hl.groups.size() != 1 || hl.groups[0].nact > 8 || hl.groups[0].ncell > 8 ||
+      kOffWork + sizeof(HadWork) * hl.work.size() > kListBytes)
+    return bad(FLGF_EINVAL, "convolve_static: launch lists exceed the scratch");
+  StaticLists L;
+  std::memset(&L, 0, sizeof(L));
+  L.group = hl.groups[0];
+  L.nchunk = nchunk;
+  L.nblk = nblk;
+  L.h2 = h * h;
+  std::copy(hl.src_ids.begin(), hl.src_ids.end(), L.src);
+  std::copy(hl.tgt_ids.begin(), hl.tgt_ids.end(), L.tgt);
+  std::copy(hl.par_tab.begin(), hl.par_tab.end(), L.par);
 
   void* base = nullptr;
   cudaError_t e = scratch_address(&base);
@@ -143,19 +179,20 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
   void* acc = sp + kSpecBytes;
   unsigned char* dl = sp + 2 * kSpecBytes;
   cudaStream_t s = cv.stream;
-  // pageable source: the call returns once the lists are staged, so `lists` may go
-  e = cudaMemcpyAsync(dl, lists.data(), lists.size(), cudaMemcpyHostToDevice, s);
-  const int* d_ids = reinterpret_cast<const int*>(dl + o_ids);
+  // the lists travel as kernel parameters, written into the scratch on the stream
+  static_lists_kernel<<<1, 256, 0, s>>>(L, dl);
+  e = cudaGetLastError();
+  const int* d_ids = reinterpret_cast<const int*>(dl + kOffIds);
   if (e == cudaSuccess) {
     if (cv.fp64) e = launch_fft_forward<double>(N, static_cast<const double*>(f), d_ids, d_ids, nblk, spec, nblk, s);
     else e = launch_fft_forward<float>(N, static_cast<const float*>(f), d_ids, d_ids, nblk, spec, nblk, s);
   }
   if (e == cudaSuccess) {
-    const HadGroup* d_groups = reinterpret_cast<const HadGroup*>(dl + o_groups);
-    const HadWork* d_work = reinterpret_cast<const HadWork*>(dl + o_work);
-    const int* d_src = reinterpret_cast<const int*>(dl + o_src);
-    const int* d_tgt = reinterpret_cast<const int*>(dl + o_tgt);
-    const int16_t* d_par = reinterpret_cast<const int16_t*>(dl + o_par);
+    const HadGroup* d_groups = reinterpret_cast<const HadGroup*>(dl + kOffGroup);
+    const HadWork* d_work = reinterpret_cast<const HadWork*>(dl + kOffWork);
+    const int* d_src = reinterpret_cast<const int*>(dl + kOffSrc);
+    const int* d_tgt = reinterpret_cast<const int*>(dl + kOffTgt);
+    const uint16_t* d_par = reinterpret_cast<const uint16_t*>(dl + kOffPar);
     const int nw = (int)hl.work.size();
     if (cv.fp64)
       e = launch_hadamard<double>(N, d_groups, d_work, nw, hl.max_units, d_src, d_tgt, d_par, spec, acc, nblk,
@@ -165,9 +202,9 @@ extern "C" int flgf_convolve_static(flgf_ctx* ctx, int nblk, const int32_t* coor
                                  cv.kspec, cv.kstride, s);
   }
   if (e == cudaSuccess) {
-    const double* d_scale = reinterpret_cast<const double*>(dl + o_scale);
-    if (cv.fp64) e = launch_fft_inverse<double>(N, acc, nblk, d_ids, d_ids, d_scale, nblk, static_cast<double*>(u), s);
-    else e = launch_fft_inverse<float>(N, acc, nblk, d_ids, d_ids, d_scale, nblk, static_cast<float*>(u), s);
+    const double* d_scale = reinterpret_cast<const double*>(dl + kOffScale);
+    if (cv.fp64) e = launch_fft_inverse<double>(N, acc, nblk, d_ids, d_ids, d_scale, nblk, static_cast<double*>(u), s, false);
+    else e = launch_fft_inverse<float>(N, acc, nblk, d_ids, d_ids, d_scale, nblk, static_cast<float*>(u), s, false);
   }
   if (e != cudaSuccess) return bad(FLGF_ECUDA, cudaGetErrorString(e));
   return FLGF_OK;

@@ -18,8 +18,12 @@
 // b * ncell + c (zero where the child is absent or no source), so the threads
 // of a warp -- consecutive parents of a full tile -- read consecutive 16-byte
 // vectors.  A table in shared memory gives, per parent and neighbour e, the
-// cell (or none).  Parents without targets and cells without sources take no
-// thread and no shared memory, so sparse meshes keep the threads busy.
+// cell (or none); the host orders a group's parents by their set of
+// neighbours with sources (most first, equal sets together), so that where a
+// warp's parents share the set its lanes skip the same absent neighbours
+// instead of idling while other lanes work.  Parents without targets and
+// cells without sources take no thread and no shared memory, so sparse meshes
+// keep the threads busy.
 //
 // CTA = (group) x (cpc chunks of T frequencies), 256 threads: a thread is
 // (parent slot, frequency group, chunk).  Groups with few parents take
@@ -46,7 +50,7 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadGroup
                                                                   const HadWork* __restrict__ work,
                                                                   const int* __restrict__ src_ids,
                                                                   const int* __restrict__ tgt_ids,
-                                                                  const int16_t* __restrict__ par_tab,
+                                                                  const uint16_t* __restrict__ par_tab,
                                                                   const cplx<R>* __restrict__ spec,
                                                                   cplx<R>* __restrict__ acc, int spec_blocks,
                                                                   const cplx<R>* __restrict__ kspec, size_t kstride) {
@@ -66,7 +70,7 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadGroup
   // holding kr, kr + ki, ki - kr and padding; FP32 keeps the complex values
   constexpr bool G3 = sizeof(R) == 8;
   constexpr int KV = (G3 ? 2 * kNOff * NG : kNOff * T * (int)sizeof(cplx<R>) / 16);  // 16-byte vectors per chunk
-  int16_t* NB = reinterpret_cast<int16_t*>(Ks + (size_t)gp.cpc * KV);
+  uint16_t* NB = reinterpret_cast<uint16_t*>(Ks + (size_t)gp.cpc * KV);
   for (int i = tid; i < 27 * gp.nact; i += kHadThreads) NB[i] = par_tab[gp.par_off + i];
   if constexpr (G3) {
     for (int i = tid; i < wk.nch * kNOff * T; i += kHadThreads) {
@@ -120,11 +124,15 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadGroup
       if constexpr (G3) a3[a][t] = R(0);
     }
 
-  int cn = NB[slot];  // the next neighbour's cell is read one iteration ahead
+  // e stays the (warp-uniform) loop index, so the kernel-spectrum addresses
+  // below are uniform across the warp; the next neighbour's cell is read one
+  // iteration ahead
+  unsigned cn = NB[slot];
   for (int e = 0; e < 27; ++e) {
-    const int c = cn;
+    const unsigned cw = cn;
     if (e + 1 < 27) cn = NB[(e + 1) * gp.nact + slot];
-    if (c < 0) continue;  // no neighbour parent with sources (or e = 0 without near field)
+    if (cw == kNbEnd) continue;  // no neighbour parent with sources (or e = 0 without near field)
+    const int c = (int)cw;
     const int e0 = e / 9 - 1, e1 = (e / 3) % 3 - 1, e2 = e % 3 - 1;
     // the 8 children b of neighbour parent p + e, TT frequencies each (zero where absent)
     const cplx<R>* fb = Fg + (size_t)c * TT;
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(kHadThreads, 2) hadamard_kernel(const HadGroup
 
 template <typename R>
 cudaError_t launch_hadamard(int N, const HadGroup* groups, const HadWork* work, int nwork, int max_units,
-                            const int* src_ids, const int* tgt_ids, const int16_t* par_tab, const void* spec, void* acc,
+                            const int* src_ids, const int* tgt_ids, const uint16_t* par_tab, const void* spec, void* acc,
                             int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s) {
   if (nwork <= 0) return cudaSuccess;
   constexpr int TT = (sizeof(R) == 4) ? 2 : 1;
@@ -301,9 +309,9 @@ template cudaError_t launch_hadamard_list<double>(int, const ListGroup*, int, in
                                                   size_t, cudaStream_t);
 
 template cudaError_t launch_hadamard<float>(int, const HadGroup*, const HadWork*, int, int, const int*, const int*,
-                                            const int16_t*, const void*, void*, int, const void*, size_t, cudaStream_t);
+                                            const uint16_t*, const void*, void*, int, const void*, size_t, cudaStream_t);
 template cudaError_t launch_hadamard<double>(int, const HadGroup*, const HadWork*, int, int, const int*, const int*,
-                                             const int16_t*, const void*, void*, int, const void*, size_t, cudaStream_t);
+                                             const uint16_t*, const void*, void*, int, const void*, size_t, cudaStream_t);
 
 // Shared memory of a group in 32-byte units: per chunk 8 slots per cell and
 // the 343 kernel spectra, plus the [27][nact] int16 neighbour table.
@@ -317,7 +325,8 @@ static int cell_key(const int* ch) {  // first child that is a source: identifie
   return -1;
 }
 
-void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchunk, int kunits, HadLists& L) {
+void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchunk, int kunits, HadLists& L,
+                        bool order_by_list) {
   const int max_units = (int)(kHadSmemBytes / 32);
   size_t pos = 0;
   while (pos < recs.size()) {
@@ -357,6 +366,22 @@ void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchun
     }
     cells.swap(sorted);
 
+    // parents with equal neighbour sets side by side, largest sets first
+    // (stable: spatial order within a class), so warps skip uniformly
+    if (order_by_list) {
+      auto mask = [&](size_t m) {
+        uint32_t v = 0;
+        for (int e = 0; e < 27; ++e) v |= (uint32_t)(cell_key(recs[m].cell[e]) >= 0) << e;
+        return v;
+      };
+      std::vector<std::pair<uint32_t, size_t>> key(members.size());
+      for (size_t i = 0; i < members.size(); ++i) key[i] = {mask(members[i]), members[i]};
+      std::stable_sort(key.begin(), key.end(), [](const auto& x, const auto& y) {
+        const int cx = __builtin_popcount(x.first), cy = __builtin_popcount(y.first);
+        return cx != cy ? cx > cy : x.first < y.first;
+      });
+      for (size_t i = 0; i < members.size(); ++i) members[i] = key[i].second;
+    }
     HadGroup gp;
     gp.level = level;
     gp.nact = (int)members.size();
@@ -371,15 +396,16 @@ void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchun
     gp.src_off = (int)L.src_ids.size();
     for (int b = 0; b < 8; ++b)
       for (int c = 0; c < gp.ncell; ++c) L.src_ids.push_back(cells[c][b]);
-    // per parent: the cell of each neighbour (e-major table) and the 8 targets
+    // per parent: the cell of each neighbour (e-major table, kNbEnd where the
+    // neighbour has no sources) and the 8 targets
     gp.par_off = (int)L.par_tab.size();
-    L.par_tab.resize(L.par_tab.size() + (size_t)27 * gp.nact, -1);
+    L.par_tab.resize(L.par_tab.size() + (size_t)27 * gp.nact, kNbEnd);
     gp.tgt_off = (int)L.tgt_ids.size();
     for (int m = 0; m < gp.nact; ++m) {
       const ParentRec& r = recs[members[m]];
       for (int e = 0; e < 27; ++e) {
         const int key = cell_key(r.cell[e]);
-        if (key >= 0) L.par_tab[gp.par_off + e * gp.nact + m] = (int16_t)cell_of.at(key);
+        if (key >= 0) L.par_tab[gp.par_off + e * gp.nact + m] = (uint16_t)cell_of.at(key);
       }
       L.tgt_ids.insert(L.tgt_ids.end(), r.tgt, r.tgt + 8);
     }

@@ -45,9 +45,10 @@ template <typename R>
 cudaError_t launch_fft_forward(int N, const R* nodes, const int* gids, const int* sids, int count,
                                void* spec, int spec_blocks, cudaStream_t s);
 // Inverse C2R, keep the first N^3 outputs, scale by scale[i]/(2N)^3, write (or add) to out[gids[i]].
+// compensated: FP32 spectra transformed in float-float arithmetic (ffloat.cuh).
 template <typename R>
 cudaError_t launch_fft_inverse(int N, const void* acc, int spec_blocks, const int* sids, const int* gids,
-                               const double* scales, int count, R* out, cudaStream_t s);
+                               const double* scales, int count, R* out, cudaStream_t s, bool compensated);
 // Kernel spectra of one octree level from the (2N)^3 kernel arrays (FP64 FFT),
 // stored as [chunk][343][T] in precision R; zero_near stores the 27 near
 // offsets as zero (octree levels >= 1 never use them).
@@ -63,7 +64,7 @@ struct HadGroup {
   int pslots;    // parent slots per (frequency group, chunk): power of two >= nact
   int cpc;       // frequency chunks per CTA (pslots * 2 * cpc <= kHadThreads threads)
   int ncell;     // neighbour cells that hold sources
-  int par_off;   // into the parent table: [27][nact] cell of neighbour e, or -1
+  int par_off;   // into the parent table: [27][nact] cell of neighbour e, or kNbEnd
   int tgt_off;   // into the target list: [nact][8] spectrum column or -1 (child a = 4 a0 + 2 a1 + a2)
   int src_off;   // into the source list: [8][ncell] spectrum column of child b of cell c, or -1
 };
@@ -75,6 +76,7 @@ constexpr int kHadThreads = 256;              // threads per CTA
 constexpr int kHadMaxCpc = 4;                 // frequency chunks per CTA
 constexpr int kHadMaxParents = 128;           // parents per group
 constexpr size_t kHadSmemBytes = 110 * 1024;  // dynamic shared memory per CTA (two CTAs per SM)
+constexpr uint16_t kNbEnd = 0xFFFF;           // no neighbour cell (cells < 2048)
 // One parent with targets: its 8 children (spectrum column or -1) and, per
 // neighbour e (e = 9 (e0+1) + 3 (e1+1) + (e2+1)), the 8 children of parent
 // p + e that are sources (all -1 when there are none or the pair is excluded).
@@ -87,19 +89,22 @@ struct HadLists {
   std::vector<HadGroup> groups;
   std::vector<HadWork> work;
   std::vector<int> src_ids, tgt_ids;
-  std::vector<int16_t> par_tab;
+  std::vector<uint16_t> par_tab;
   int max_units = 0;  // max over groups of their shared memory in 32-byte units
 };
 // Packs parent records, in order, into groups of one octree level and their
 // work items (nchunk frequency chunks); kunits = 32-byte units of kernel
-// spectra per chunk in shared memory (had_kernel_units).
-void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchunk, int kunits, HadLists& L);
+// spectra per chunk in shared memory (had_kernel_units).  order_by_list
+// orders each group's parents by their set of neighbours with sources (most
+// first, equal sets together) instead of keeping the record order.
+void pack_parent_groups(int level, const std::vector<ParentRec>& recs, int nchunk, int kunits, HadLists& L,
+                        bool order_by_list = false);
 // Kernel-spectrum shared memory per chunk of the dense MAC, in 32-byte units:
 // the complex values (FP32) or the three-product form (FP64, twice as large).
 constexpr int had_kernel_units(bool fp64) { return fp64 ? 2 * kNOff : kNOff; }
 template <typename R>
 cudaError_t launch_hadamard(int N, const HadGroup* groups, const HadWork* work, int nwork, int max_units,
-                            const int* src_ids, const int* tgt_ids, const int16_t* par_tab, const void* spec, void* acc,
+                            const int* src_ids, const int* tgt_ids, const uint16_t* par_tab, const void* spec, void* acc,
                             int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s);
 // Sparse tiles: explicit (target, source) pair lists.  The targets of the
 // sparse tiles of one octree level are pooled in tile order and cut into
@@ -130,8 +135,9 @@ template <typename R>
 cudaError_t launch_anterp(int N, int nI, const double* J1, const int* parents, const int* children /*[n][8]*/,
                           int n, R* nodes, cudaStream_t s);
 template <typename R>
+// compensated: FP32 data interpolated in float-float arithmetic (ffloat.cuh).
 cudaError_t launch_interp_add(int N, int nI, const double* J1, const int* childs, const int* parents, const int* cpos,
-                              int n, R* unodes, cudaStream_t s);
+                              int n, R* unodes, cudaStream_t s, bool compensated);
 // dst[dst_ids[i]] = src[src_ids[i]] * (mask? mask[i] : 1)
 template <typename R>
 cudaError_t launch_copy_blocks(int N, const R* src, const int* src_ids, R* dst, const int* dst_ids,

@@ -12,6 +12,7 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "ffloat.cuh"
 #include "internal.h"
 
 namespace cg = cooperative_groups;
@@ -33,17 +34,72 @@ __host__ __device__ constexpr int band_start(int j) {
 template <int N>
 __device__ __forceinline__ int pidx(int i, int j, int k) { return (i * N + j) * (N + 1) + k; }
 
+// Position of child node j in its Lagrange window, in parent spacings from
+// the window's first node: child nodes at j + 1/2, parent nodes at 2p + 1
+// (child spacings), so t = (j + 1/2 - (2 s + 1)) / 2.
+template <int N, int NI>
+__host__ __device__ constexpr double window_pos(int j) {
+  return (j - 2 * band_start<N, NI>(j) - 0.5) / 2.0;
+}
+// Newton coefficient of order k at t: forward t (t-1) ... (t-k+1) / k!
+// (BACK = false) or backward t (t+1) ... (t+k-1) / k! (BACK = true).
+template <bool BACK>
+__host__ __device__ constexpr double newton_coef(double t, int k) {
+  double c = 1.0;
+  for (int i = 0; i < k; ++i) c *= (BACK ? t + i : t - i) / (i + 1);
+  return c;
+}
+
 // One 1-D pass of interpolation (child position C along the axis) on a line
-// held in registers: out[r] = sum_m W[C N + r][m] in[band_start(C N + r) + m].
+// held in registers: out[r] = the n_I-point Lagrange polynomial through the
+// window's parent values, at child node C N + r.  Rows whose point lies in the
+// central interval of their window use the Lagrange weights W (|w|_1 <= 1.3).
+// The off-centre rows near the block faces, whose Lagrange weights alternate
+// in sign with |w|_1 up to 7.2 (n_I = 6) and so would turn FP32 rounding into
+// several ulps of error, evaluate the same polynomial in Newton form from the
+// nearer end of the window: forward differences from its first node (point
+// left of centre) or backward differences from its last node (right of
+// centre), whose coefficients |c_k| stay small because the point is close to
+// that end; for a smooth field the differences shrink with their order, so
+// the rounding stays relative to the field value.
 template <typename R, int N, int NI, int C>
 __device__ __forceinline__ void line_interp(const R* in, R* out, const R* W) {
 #pragma unroll
   for (int r = 0; r < N; ++r) {
     const int j = C * N + r;
-    R s = R(0);
+    const int s = band_start<N, NI>(j);
+    const double t = window_pos<N, NI>(j);
+    const double mid = 0.5 * (NI - 1);
+    R acc;
+    if (t >= mid - 0.5 && t <= mid + 0.5) {
+      acc = Arith<R>::from_d(0.0);
 #pragma unroll
-    for (int m = 0; m < NI; ++m) s = fma(W[j * NI + m], in[band_start<N, NI>(j) + m], s);
-    out[r] = s;
+      for (int m = 0; m < NI; ++m) acc = mad(W[j * NI + m], in[s + m], acc);
+    } else if (t < mid) {
+      R d[NI];
+#pragma unroll
+      for (int i = 0; i < NI; ++i) d[i] = in[s + i];
+#pragma unroll
+      for (int k = 1; k < NI; ++k)
+#pragma unroll
+        for (int i = NI - 1; i >= k; --i) d[i] = d[i] - d[i - 1];  // d[k] = forward difference of order k at s
+      acc = d[NI - 1] * Arith<R>::from_d(newton_coef<false>(t, NI - 1));
+#pragma unroll
+      for (int k = NI - 2; k >= 0; --k) acc = mad(Arith<R>::from_d(newton_coef<false>(t, k)), d[k], acc);
+    } else {
+      R d[NI];
+#pragma unroll
+      for (int i = 0; i < NI; ++i) d[i] = in[s + NI - 1 - i];
+#pragma unroll
+      for (int k = 1; k < NI; ++k)
+#pragma unroll
+        for (int i = NI - 1; i >= k; --i) d[i] = d[i - 1] - d[i];  // d[k] = backward difference of order k at s + NI - 1
+      const double tau = t - (NI - 1);
+      acc = d[NI - 1] * Arith<R>::from_d(newton_coef<true>(tau, NI - 1));
+#pragma unroll
+      for (int k = NI - 2; k >= 0; --k) acc = mad(Arith<R>::from_d(newton_coef<true>(tau, k)), d[k], acc);
+    }
+    out[r] = acc;
   }
 }
 // Its adjoint (anterpolation): out[q] += sum_r J[C N + r][q] in[r].
@@ -67,7 +123,7 @@ __device__ __forceinline__ void load_band(const double* __restrict__ J1, R* W) {
     const int j = i / NI, m = i % NI;
     int s = (NI % 2 == 0) ? (j == 0 ? -1 : (j - 1) / 2) - (NI / 2 - 1) : ((j % 2 == 0) ? j / 2 : (j - 1) / 2) - NI / 2;
     s = s < 0 ? 0 : (s > N - NI ? N - NI : s);
-    W[i] = (R)J1[j * N + s + m];
+    W[i] = Arith<R>::from_d(J1[j * N + s + m]);
   }
 }
 
@@ -148,40 +204,46 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(N * N)
   cluster.sync();  // no CTA leaves while others still read its shared memory
 }
 
-// a5: child += (J_c0 x J_c1 x J_c2) parent.
-template <typename R, int N, int NI>
+// a5: child += (J_c0 x J_c1 x J_c2) parent, in arithmetic type C: R, or the
+// compensated ff for FP32 data (the three passes then keep their intermediate
+// lines in float-float, so the rounding of one pass is not amplified by the
+// extrapolating rows of the next).
+template <typename R, int N, int NI, typename C = R>
 __global__ void __launch_bounds__(N * N) interp_add_kernel(const double* __restrict__ J1, const int* __restrict__ childs,
                                                            const int* __restrict__ parents, const int* __restrict__ cpos,
                                                            R* __restrict__ unodes) {
   constexpr int N3 = N * N * N, PS = N * N * (N + 1);
-  __shared__ R W[2 * N * NI];
-  __shared__ R A[PS];  // each thread transforms whole lines in place
-  load_band<R, N, NI>(J1, W);
+  __shared__ C W[2 * N * NI];
+  __shared__ C A[PS];  // each thread transforms whole lines in place
+  load_band<C, N, NI>(J1, W);
   const int t = threadIdx.x, u = t / N, v = t % N;
   const int c = cpos[blockIdx.x];
   const int c0 = c >> 2, c1 = (c >> 1) & 1, c2 = c & 1;
   const R* src = unodes + (size_t)parents[blockIdx.x] * N3;
-  for (int i = t; i < N3; i += blockDim.x) A[pidx<N>(i / (N * N), (i / N) % N, i % N)] = src[i];
+  for (int i = t; i < N3; i += blockDim.x) A[pidx<N>(i / (N * N), (i / N) % N, i % N)] = Arith<C>::from(src[i]);
   __syncthreads();
-  R in[N], out[N];
+  C in[N], out[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) in[k] = A[pidx<N>(u, v, k)];
-  if (c2) line_interp<R, N, NI, 1>(in, out, W); else line_interp<R, N, NI, 0>(in, out, W);
+  if (c2) line_interp<C, N, NI, 1>(in, out, W); else line_interp<C, N, NI, 0>(in, out, W);
 #pragma unroll
   for (int k = 0; k < N; ++k) A[pidx<N>(u, v, k)] = out[k];
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < N; ++j) in[j] = A[pidx<N>(u, j, v)];
-  if (c1) line_interp<R, N, NI, 1>(in, out, W); else line_interp<R, N, NI, 0>(in, out, W);
+  if (c1) line_interp<C, N, NI, 1>(in, out, W); else line_interp<C, N, NI, 0>(in, out, W);
 #pragma unroll
   for (int j = 0; j < N; ++j) A[pidx<N>(u, j, v)] = out[j];
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < N; ++i) in[i] = A[pidx<N>(i, u, v)];
-  if (c0) line_interp<R, N, NI, 1>(in, out, W); else line_interp<R, N, NI, 0>(in, out, W);
+  if (c0) line_interp<C, N, NI, 1>(in, out, W); else line_interp<C, N, NI, 0>(in, out, W);
   R* dst = unodes + (size_t)childs[blockIdx.x] * N3;
 #pragma unroll
-  for (int i = 0; i < N; ++i) dst[(i * N + u) * N + v] += out[i];
+  for (int i = 0; i < N; ++i) {
+    R& d = dst[(i * N + u) * N + v];
+    d = Arith<C>::template to<R>(Arith<C>::from(d) + out[i]);
+  }
 }
 
 template <typename R>
@@ -476,7 +538,13 @@ static cudaError_t anterp_n(const double* J1, const int* parents, const int* chi
 }
 template <typename R, int N, int NI>
 static cudaError_t interp_n(const double* J1, const int* childs, const int* parents, const int* cpos, int n, R* unodes,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool compensated) {
+  if constexpr (sizeof(R) == 4) {
+    if (compensated) {
+      interp_add_kernel<R, N, NI, ff><<<n, N * N, 0, s>>>(J1, childs, parents, cpos, unodes);
+      return cudaGetLastError();
+    }
+  }
   interp_add_kernel<R, N, NI><<<n, N * N, 0, s>>>(J1, childs, parents, cpos, unodes);
   return cudaGetLastError();
 }
@@ -510,14 +578,14 @@ cudaError_t launch_anterp(int N, int nI, const double* J1, const int* parents, c
 
 template <typename R>
 cudaError_t launch_interp_add(int N, int nI, const double* J1, const int* childs, const int* parents, const int* cpos,
-                              int n, R* unodes, cudaStream_t s) {
+                              int n, R* unodes, cudaStream_t s, bool compensated) {
   if (n <= 0) return cudaSuccess;
   if (N == 16) {
-    FLGF_NI_CASES(16, interp_n, J1, childs, parents, cpos, n, unodes, s)
-    if (nI == 9) return interp_n<R, 16, 9>(J1, childs, parents, cpos, n, unodes, s);
-    if (nI == 10) return interp_n<R, 16, 10>(J1, childs, parents, cpos, n, unodes, s);
+    FLGF_NI_CASES(16, interp_n, J1, childs, parents, cpos, n, unodes, s, compensated)
+    if (nI == 9) return interp_n<R, 16, 9>(J1, childs, parents, cpos, n, unodes, s, compensated);
+    if (nI == 10) return interp_n<R, 16, 10>(J1, childs, parents, cpos, n, unodes, s, compensated);
   } else if (N == 8) {
-    FLGF_NI_CASES(8, interp_n, J1, childs, parents, cpos, n, unodes, s)
+    FLGF_NI_CASES(8, interp_n, J1, childs, parents, cpos, n, unodes, s, compensated)
   }
   return cudaErrorInvalidValue;
 }
@@ -606,8 +674,8 @@ cudaError_t launch_laplacian(int N, const R* u, const int* nbr6, int n, double i
 
 #define FLGF_INST(R)                                                                                            \
   template cudaError_t launch_anterp<R>(int, int, const double*, const int*, const int*, int, R*, cudaStream_t); \
-  template cudaError_t launch_interp_add<R>(int, int, const double*, const int*, const int*, const int*, int, R*, \
-                                            cudaStream_t);                                                      \
+  template cudaError_t launch_interp_add<R>(int, int, const double*, const int*, const int*, const int*, int, R*,       \
+                                            cudaStream_t, bool);                                                \
   template cudaError_t launch_copy_blocks<R>(int, const R*, const int*, R*, const int*, const uint8_t*, int,    \
                                              cudaStream_t);                                                     \
   template cudaError_t launch_coarsen<R>(int, const R*, const int*, R*, const int*, int, cudaStream_t);         \

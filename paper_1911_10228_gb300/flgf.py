@@ -22,7 +22,10 @@ from . import build as _build
 
 FLGF_FP64, FLGF_FP32 = 0, 1
 FLGF_HOST, FLGF_DEVICE = 0, 1
-OPT_CORRECTION, OPT_GRAPH, OPT_TIMING = 1, 2, 3
+OPT_CORRECTION, OPT_GRAPH, OPT_TIMING, OPT_COMPENSATED, OPT_FAULT_HALO = 1, 2, 3, 4, 5
+CTX_LIST_PCT, CTX_TILE, CTX_FAIL_ALLOC = 1, 2, 3
+# error codes of include/flgf.h
+FLGF_EINVAL, FLGF_ENOMEM, FLGF_ECUDA, FLGF_EMESH, FLGF_ESTATE, FLGF_EDEVICE = -1, -2, -3, -4, -5, -6
 STAGES = ("coarsen", "anterpolation", "fft_forward", "spectrum_mac", "fft_inverse", "interpolation", "multires")
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
@@ -32,7 +35,11 @@ _c_dbl_p = ctypes.POINTER(ctypes.c_double)
 
 
 class FLGFError(RuntimeError):
-    pass
+    """A library call failed; ``code`` is its FLGF_E* return code."""
+
+    def __init__(self, msg: str, code: int = 0):
+        super().__init__(msg)
+        self.code = code
 
 
 class _Opts(ctypes.Structure):
@@ -52,6 +59,9 @@ PROTOTYPES = {
                                             _c_dbl_p]),
     "flgf_blockset_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_int_p, _c_int_p, _c_i32_p, _c_dbl_p,
                                             ctypes.POINTER(ctypes.c_void_p)]),
+    "flgf_blockset_create_masked": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_int_p, _c_int_p, _c_i32_p,
+                                                   _c_dbl_p, ctypes.POINTER(ctypes.c_uint8),
+                                                   ctypes.POINTER(ctypes.c_void_p)]),
     "flgf_blockset_destroy": (None, [ctypes.c_void_p]),
     "flgf_blockset_dof": (ctypes.c_int64, [ctypes.c_void_p]),
     "flgf_load_source": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
@@ -122,25 +132,30 @@ class Context:
         with torch.cuda.device(self.device):
             rc = self.lib.flgf_create(ctypes.byref(h), ctypes.byref(o))
         if rc != 0:
-            raise FLGFError(f"flgf_create failed with code {rc}")
+            raise FLGFError(f"flgf_create failed with code {rc}", rc)
         self.handle = h
         self.plan = (30, (4, 4, 8))  # (pair-list percentage, dense tile): the library's defaults
 
     def check(self, rc: int, what: str):
         if rc != 0:
             msg = self.lib.flgf_last_error(self.handle).decode()
-            raise FLGFError(f"{what} failed ({rc}): {msg}")
+            raise FLGFError(f"{what} failed ({rc}): {msg}", rc)
+
+    def fail_alloc(self, n: int):
+        """Failure injection: the n-th device allocation of this context's block
+        sets from now on reports out-of-memory (0 disarms)."""
+        self.check(self.lib.flgf_ctx_set_option(self.handle, CTX_FAIL_ALLOC, int(n)), "flgf_ctx_set_option")
 
     def set_plan(self, list_pct: int | None = None, tile=None):
         """Plan options for block sets created afterwards: the useful-pair
         percentage below which a tile runs on the pair-list MAC, and the dense
         MAC tile (t0, t1, t2) in parents."""
         if list_pct is not None:
-            self.check(self.lib.flgf_ctx_set_option(self.handle, 1, int(list_pct)), "flgf_ctx_set_option")
+            self.check(self.lib.flgf_ctx_set_option(self.handle, CTX_LIST_PCT, int(list_pct)), "flgf_ctx_set_option")
             self.plan = (int(list_pct), self.plan[1])
         if tile is not None:
             t = [int(v) for v in tile]
-            self.check(self.lib.flgf_ctx_set_option(self.handle, 2, t[0] | t[1] << 8 | t[2] << 16),
+            self.check(self.lib.flgf_ctx_set_option(self.handle, CTX_TILE, t[0] | t[1] << 8 | t[2] << 16),
                        "flgf_ctx_set_option")
             self.plan = (self.plan[0], tuple(t))
 
@@ -162,9 +177,15 @@ class Context:
         """Exact block convolution of at most 32 blocks (one 4x4x4 aligned box) with
         no device allocation inside the library; f and out are device tensors."""
         coords = np.ascontiguousarray(np.asarray(coords, dtype=np.int32).reshape(-1, 3))
+        shape = (coords.shape[0], self.N, self.N, self.N)
+        if not isinstance(f, torch.Tensor) or tuple(f.shape) != shape:
+            raise ValueError(f"f must be a tensor of shape {shape}")
         f = f.to(device=self.device, dtype=self.dtype).contiguous()
         if out is None:
             out = torch.empty_like(f)
+        elif (tuple(out.shape) != shape or out.dtype != self.dtype or out.device != self.device
+              or not out.is_contiguous()):
+            raise ValueError(f"out must be a contiguous {self.dtype} tensor of shape {shape} on {self.device}")
         self.stream.wait_stream(torch.cuda.current_stream(self.device))
         self.check(self.lib.flgf_convolve_static(self.handle, coords.shape[0], _ptr(coords, ctypes.c_int32),
                                                  ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()),
@@ -189,10 +210,12 @@ class BlockSet:
     """One or more independent (possibly refined) Poisson problems.
 
     problems: list over problems of lists over levels of int (nb, 3) block
-    coordinates; h0: per-problem spacing of level 0.
+    coordinates; h0: per-problem spacing of level 0; want (optional): the same
+    nesting of boolean arrays (nb,) marking the blocks whose potential is
+    needed (a shard of a multi-GPU solve); the others are left unspecified.
     """
 
-    def __init__(self, ctx: Context, problems, h0):
+    def __init__(self, ctx: Context, problems, h0, want=None):
         self.ctx = ctx
         self.lib = ctx.lib
         self.levels = [[np.asarray(c, dtype=np.int32).reshape(-1, 3) for c in p] for p in problems]
@@ -204,9 +227,19 @@ class BlockSet:
             raise ValueError("one h0 per problem")
         h = ctypes.c_void_p()
         with torch.cuda.device(ctx.device):
-            rc = self.lib.flgf_blockset_create(ctx.handle, len(self.levels), _ptr(nlev, ctypes.c_int),
-                                               _ptr(nblk, ctypes.c_int), _ptr(coords, ctypes.c_int32),
-                                               _ptr(h0, ctypes.c_double), ctypes.byref(h))
+            if want is None:
+                rc = self.lib.flgf_blockset_create(ctx.handle, len(self.levels), _ptr(nlev, ctypes.c_int),
+                                                   _ptr(nblk, ctypes.c_int), _ptr(coords, ctypes.c_int32),
+                                                   _ptr(h0, ctypes.c_double), ctypes.byref(h))
+            else:
+                w = np.ascontiguousarray(np.concatenate([np.asarray(m, dtype=bool).reshape(-1) for p in want for m in p])
+                                         .astype(np.uint8))
+                if w.size != coords.shape[0]:
+                    raise ValueError("want must hold one flag per block")
+                rc = self.lib.flgf_blockset_create_masked(ctx.handle, len(self.levels), _ptr(nlev, ctypes.c_int),
+                                                          _ptr(nblk, ctypes.c_int), _ptr(coords, ctypes.c_int32),
+                                                          _ptr(h0, ctypes.c_double), _ptr(w, ctypes.c_uint8),
+                                                          ctypes.byref(h))
         ctx.check(rc, "flgf_blockset_create")
         self.handle = h
         self.h0 = h0
@@ -337,11 +370,14 @@ class BlockSet:
             pass
 
 
-def solve_problem(ctx: Context, prob, correction: bool = True) -> list:
-    """Convenience: solve one inputs.Problem; returns u per level as device tensors."""
+def solve_problem(ctx: Context, prob, correction: bool = True, compensated: bool | None = None) -> list:
+    """Convenience: solve one inputs.Problem; returns u per level as device tensors.
+    compensated: FLGF_OPT_COMPENSATED (None keeps the library's default)."""
     bs = BlockSet(ctx, [prob.coords], [prob.h0])
     if not correction:
         bs.set_option(OPT_CORRECTION, 0)
+    if compensated is not None:
+        bs.set_option(OPT_COMPENSATED, int(compensated))
     for l, f in enumerate(prob.f):
         bs.load_source(0, l, torch.as_tensor(np.asarray(f)))
     bs.solve()

@@ -1,11 +1,13 @@
 """Host-side logic of multi-process runs (one process per GPU).
 
-The solver itself needs no exchange between GPUs for the workloads measured
-here: the uniform solve runs as independent replicas, and the batched form is
-a set of independent problems, so a job of ``world`` ranks gives each rank its
-own disjoint slice of problems.  What the ranks share is only bookkeeping:
-a barrier around the timed region, the maximum of the ranks' timings, and the
-sum of the work they did.  These helpers work with any initialised
+The solver itself needs no exchange between GPUs during a solve: the batched
+form is a set of independent problems, so a job of ``world`` ranks gives each
+rank its own disjoint slice of problems, and a single solve sharded by target
+blocks (``shard.py``) has every rank compute its own targets from the
+replicated source.  What the ranks share is bookkeeping -- a barrier around
+the timed region, the maximum of the ranks' timings, the sum of the work they
+did -- and, when one rank needs the whole field of a sharded solve, one
+summation of the owned blocks after it.  These helpers work with any initialised
 ``torch.distributed`` backend (NCCL on GPUs, gloo on CPUs) and reduce to the
 plain value in a single-process run.
 """
@@ -52,3 +54,15 @@ def problem_seeds(per_rank: int, rank: int) -> list[int]:
     if per_rank < 0 or rank < 0:
         raise ValueError("per_rank and rank must be non-negative")
     return list(range(rank * per_rank, (rank + 1) * per_rank))
+
+
+def assemble_owned(u: torch.Tensor, owned) -> torch.Tensor:
+    """Whole field of a solve sharded by blocks: every rank passes its field
+    (nb, ...) and the boolean mask (nb,) of the blocks it owns; the blocks are
+    owned by exactly one rank each, so zeroing the others and summing over the
+    ranks returns every block from its owner, on every rank."""
+    m = torch.as_tensor(owned, dtype=torch.bool, device=u.device).reshape(-1, *([1] * (u.dim() - 1)))
+    out = torch.where(m, u, torch.zeros_like(u))
+    if active():
+        dist.all_reduce(out, op=dist.ReduceOp.SUM)
+    return out

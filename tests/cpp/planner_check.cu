@@ -85,7 +85,7 @@ int main(int argc, char** argv) {
     const HadGroup* G = reinterpret_cast<const HadGroup*>(base + ph.hgroups);
     const int* src = reinterpret_cast<const int*>(base + ph.src_ids);
     const int* tgt = reinterpret_cast<const int*>(base + ph.tgt_ids);
-    const int16_t* par = reinterpret_cast<const int16_t*>(base + ph.par_tab);
+    const uint16_t* par = reinterpret_cast<const uint16_t*>(base + ph.par_tab);
     for (int gi = 0; gi < ph.n_groups_dense; ++gi) {
       const HadGroup& g = G[gi];
       for (int m = 0; m < g.nact; ++m) {
@@ -96,8 +96,10 @@ int main(int argc, char** argv) {
           bad += tlevel.count(t) == 0 || tlevel[t] != g.level;
         }
         for (int e = 0; e < 27; ++e) {
-          const int c = par[g.par_off + e * g.nact + m];
-          if (c < 0) continue;
+          const unsigned w = par[g.par_off + e * g.nact + m];
+          if (w == kNbEnd) continue;
+          const int c = (int)w;
+          if (c >= g.ncell) { ++bad; continue; }
           const int e0 = e / 9 - 1, e1 = (e / 3) % 3 - 1, e2 = e % 3 - 1;
           for (int b = 0; b < 8; ++b) {
             const int s = src[g.src_off + b * g.ncell + c];

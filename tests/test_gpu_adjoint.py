@@ -32,11 +32,10 @@ def _adjoint_gpu(c, p, g, correction=True):
     return out
 
 
-# FP32 with the source correction: the correction subtracts a 7-point Laplacian
-# (x 1/h^2) of the FP32 coarse field, which amplifies its rounding into the
-# finer levels' sources; measured ~2e-5 (3e-6 without the correction).
+# FP32 (compensated coarse octree levels, the default on refined meshes):
+# measured 4.3e-6 with the source correction, 1.3e-6 without.
 @pytest.mark.parametrize("precision,correction,tol", [("fp64", True, 1e-10), ("fp64", False, 1e-10),
-                                                      ("fp32", False, 1e-5), ("fp32", True, 1e-4)])
+                                                      ("fp32", False, 1e-5), ("fp32", True, 1e-5)])
 def test_adjoint_matches_oracle(G, precision, correction, tol):
     p = _mesh()
     rng = np.random.default_rng(21)
@@ -134,6 +133,11 @@ def test_autograd_gradient_linked_tori_against_finite_differences():
     for l in range(p.n_levels):
         err = np.max(np.abs(grads["fp32"][l] - grads["fp64"][l])) / gmax
         print(f"linked tori gradient level {l}: FP32 vs FP64 rel err {err:.3e}")
-        assert err < 2e-4, (l, err)  # FP32 with the source correction (see test_adjoint_matches_oracle)
+        # The FP32 adjoint is held to 1e-4, the bound the hot-path contract sets for
+        # it: the transposed source correction applies the 7-point stencil (x
+        # 1/h^2) to the finer level's FP32 adjoint field, which amplifies its
+        # rounding into the coarsest level's gradient (measured 2.4e-5 there,
+        # 3e-6 and 2e-7 on the finer levels).
+        assert err < 1e-4, (l, err)
     bs64.close()
     c64.close()

@@ -20,7 +20,8 @@ PLANS = [None, (0, (4, 4, 8)), (100, (2, 4, 8)), (50, (4, 4, 4))]
 
 
 @pytest.mark.parametrize("plan", PLANS, ids=["default", "dense", "list", "mixed"])
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+# FP32: within 1e-5 of the FP64 oracle (measured 8e-7 to 1e-6 on these problems)
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_random_sparse_batch_matches_oracle(G, precision, tol, plan):
     probs = [random_sparse_problem(s, N=8, nblk_range=(8, 120)) for s in (1, 4, 7, 9)]
     assert max(p.n_levels for p in probs) >= 2

@@ -9,7 +9,8 @@
   on the leaf interior of every level up to the precision of the FMM (Sec. 3,
   consistency with the source correction; measured with n_I = 6: 7e-6, 2e-5,
   2e-4 of max|f| on levels 0, 1, 2, the FMM error amplified by 1/h^2), and
-  the FP32 form agrees with the FP64 solve.
+  the FP32 form agrees with the FP64 solve and with the FP64 oracle at
+  sampled cells (tests/golden/torus128_oracle.txt) within 1e-5.
 """
 import numpy as np
 import pytest
@@ -92,8 +93,9 @@ def test_torus_multires_laplacian_consistency_and_fp32():
         b = u64[l].cpu().numpy()[leaf[l]]
         err = rel(a, b)
         print(f"torus level {l}: FP32 vs FP64 rel err {err:.3e}")
-        # FP32 with the source correction (a 1/h^2-scaled stencil of FP32 fields): 1e-4
-        assert err < 1e-4, (l, err)
+        # FP32 (compensated coarse octree levels, the default on refined meshes):
+        # measured 1.3e-6, 2.5e-6, 7.4e-6 on levels 0, 1, 2
+        assert err < 1e-5, (l, err)
     bs.close()
     c64.close()
     c32.close()
@@ -111,7 +113,7 @@ def test_batched_full_size_sampled_problems_match_oracle():
     size = lambda i: sum(len(c) for c in probs[i].coords)
     small = [min((i for i in range(len(probs)) if probs[i].n_levels == L), key=size) for L in (1, 2, 3)]
     refs = {i: multires_solve(LGF(), probs[i].coords, probs[i].f, 16, 6, probs[i].h0) for i in small}
-    for precision, tol in (("fp64", 1e-10), ("fp32", 1e-4)):
+    for precision, tol in (("fp64", 1e-10), ("fp32", 1e-5)):
         ctx = F.Context(N=16, n_interp=6, precision=precision)
         ctx.set_plan(list_pct=30, tile=(4, 4, 4))
         bs = F.BlockSet(ctx, [p.coords for p in probs], [p.h0 for p in probs])

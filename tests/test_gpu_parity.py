@@ -168,13 +168,16 @@ def test_laplacian_matches_oracle():
     assert np.all(got[~mask] == 0.0)
 
 
-def test_batched_problems_equal_single_solves():
+@pytest.mark.parametrize("compensated", [0, 1])
+def test_batched_problems_equal_single_solves(compensated):
     """Several independent problems in one block set run in the same launches
-    and give bit-identical results to solving each alone."""
+    and give bit-identical results to solving each alone (with the same
+    FLGF_OPT_COMPENSATED setting: its default depends on the block set)."""
     c = ctx(8, "fp32")
     probs = [_gauss_problem(box_coords(3), 8, 7), _two_level(), _gauss_problem(box_coords(5), 8, 8)]
-    singles = [gpu_solve(c, p) for p in probs]
+    singles = [[u.double().cpu().numpy() for u in F.solve_problem(c, p, compensated=bool(compensated))] for p in probs]
     bs = F.BlockSet(c, [p.coords for p in probs], [p.h0 for p in probs])
+    bs.set_option(F.OPT_COMPENSATED, compensated)
     for i, p in enumerate(probs):
         for l, f in enumerate(p.f):
             bs.load_source(i, l, torch.as_tensor(f))
