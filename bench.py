@@ -1,21 +1,29 @@
 #!/usr/bin/env python
-"""Benchmark of the FLGF Poisson solve (arXiv:1911.10228) on one GB300.
+"""Benchmark of the FLGF Poisson solve (arXiv:1911.10228) on GB300.
 
-Workload: the 256^3 uniform lattice as 16^3 blocks of 16^3 cells, octree
-levels 0..2 (+ root), Lagrange n_I = 6, source = 16 seeded Gaussians (sigma
-3-10 cells, centres in the inner 128^3 region, amplitudes U(-1, 1)).  One
-step = one full solve (anterpolation, forward FFTs, spectrum MAC, inverse
-FFTs, interpolation) with the source already resident in HBM; L2 is flushed
+Headline workload: the batched form -- 64 independent random sparse problems
+of 16^3 blocks (block counts log-uniform in [8, 4096] over 1-3 refinement
+levels, 1-4 Gaussians each, seeds 64 r .. 64 r + 63 on rank r) in one block
+set, every stage of every problem in the same kernel launches, the solve
+replayed as a CUDA graph.  One step = one full multi-resolution solve of the
+batch (Sec. 3: coarsening, per level the FLGF of Sec. 2.1 -- anterpolation,
+forward FFTs, spectrum multiply-accumulate, inverse FFTs, interpolation --
+and the coarse-fine coupling) with the sources resident in HBM; L2 is flushed
 (256 MB write) before every timed step.  The headline value is the FP32
-form's DoF/s; the plain FP64 solve is timed on the same GPU beside it and
-both are checked against the FP64 CPU oracle on sampled target blocks.
+form's DoF/s (leaf cells per second); the plain FP64 solve of the same batch
+is timed beside it, and the FP32 error is stated against it and, on a sample
+of problems, against the FP64 CPU oracle.
+
+Further legs (keys of the JSON line): the 256^3 uniform lattice (16^3 blocks,
+n_I = 6), the 3-level torus with the FP32 compensation off and on, the
+adjoint solve on the linked tori, and the end-to-end batched solve through the
+C ABI with host buffers.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-With N > 1 (torchrun) every rank solves its own replica (the workload does
-not shard without a halo exchange); value = all ranks' DoF / max rank time.
-``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
-workload instead.
+With N > 1 (torchrun) every rank solves its own 64 problems (no exchange):
+value = all ranks' DoF / slowest rank's time.  ``--impl reference`` times the
+FP64 CPU oracle on bounded samples of the batched workload instead.
 """
 from __future__ import annotations
 
@@ -34,12 +42,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Poisson DoF/s at stated rel err: FP32 batched vs FP64 plain; % HBM roofline"
-WORKLOAD = ("uniform 256^3 lattice, 16^3 blocks of 16^3 cells, octree levels 0-2 + root, n_I=6, "
-            "16 Gaussians sigma 3-10 cells in the inner 128^3, seed 0")
-N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_ALU_PEAK_TFLOPS = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
+BATCH_WORKLOAD = ("batched: 64 independent random sparse problems per GPU (seeds 64 r .. 64 r + 63 on rank r), "
+                  "16^3 blocks, block counts log-uniform in [8, 4096] over 1-3 refinement levels, 1-4 Gaussians "
+                  "each, n_I = 6, one block set, CUDA graph")
+UNIFORM_WORKLOAD = ("uniform 256^3 lattice, 16^3 blocks of 16^3 cells, octree levels 0-2 + root, n_I=6, "
+                    "16 Gaussians sigma 3-10 cells in the inner 128^3, seed 0")
+FP32_LANES = 128          # FP32 FMA lanes per SM
 FP64_NOMINAL_TFLOPS = 1.25
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_SM_MHZ = 2070.0
 
 
 def args_parse():
@@ -48,12 +59,13 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=64, help="target blocks in the oracle sample")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--problems", type=int, default=64, help="problems of the batched workload per GPU")
+    ap.add_argument("--legs", default="batched,uniform,multires,adjoint",
+                    help="legs to run; the batched leg (the headline) always runs")
     ap.add_argument("--precisions", default="fp32,fp64", help="contexts to time (profiling runs use fp32)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle budget of the cpu_baseline sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched leg")
-    ap.add_argument("--no-multires", action="store_true", help="skip the refined-mesh and adjoint legs")
     ap.add_argument("--plan", default=None,
                     help="fixed MAC plan for the batched leg, e.g. 30/4x4x4 (list percentage / tile); default: autotune")
     return ap.parse_args()
@@ -66,8 +78,8 @@ def peaks():
             d = json.load(f)
         for key in ("hbm_gbs", "hbm_GBs", "hbm"):
             if key in d:
-                return float(d[key]), "measured"
-    return FALLBACK_HBM_GBS, "fallback"
+                return float(d[key]), "measured", float(d.get("sm_max_mhz", FALLBACK_SM_MHZ))
+    return FALLBACK_HBM_GBS, "fallback", FALLBACK_SM_MHZ
 
 
 class ClockSampler:
@@ -127,9 +139,9 @@ def file_sha(path):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def ncu_traffic(kernel_src: str, kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+def ncu_traffic(kernel_src: str, kernel: str, workload: str):
+    """DRAM bytes per step of a kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -139,225 +151,238 @@ def ncu_traffic(kernel_src: str, kernel: str):
             if line.startswith("#") or not line.strip():
                 continue
             kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
-            if kv.get("kernel") == kernel and kv.get("src_sha") == sha and kv.get("workload") == "uniform256":
-                return float(kv["dram_bytes_per_launch"])
+            if kv.get("kernel") == kernel and kv.get("src_sha") == sha and kv.get("workload") == workload:
+                return float(kv["dram_bytes"])
     return None
 
 
-def oracle_sample(prob, n_sample: int, seed: int = 0):
-    """FP64 oracle on a sample of target blocks; returns (targets, u_on_targets, seconds, setup_seconds)."""
-    from oracle.flgf import FLGF
+def leaf_linf(outs_a, outs_b, probs):
+    """max over problems and leaf cells of |a - b|, over max |b| (per problem)."""
+    import torch
+    worst = 0.0
+    for ua, ub, p in zip(outs_a, outs_b, probs):
+        num, den = 0.0, 0.0
+        for xa, xb, lm in zip(ua, ub, p.leaf_masks()):
+            if not lm.any():
+                continue
+            m = torch.as_tensor(lm, device=xb.device)
+            num = max(num, float((xa.double() - xb.double())[m].abs().max()))
+            den = max(den, float(xb.double()[m].abs().max()))
+        worst = max(worst, num / den if den > 0 else 0.0)
+    return worst
+
+
+def oracle_batch_sample(probs, budget_s: float):
+    """FP64 oracle (multi-resolution solve) on the smallest problems of the
+    batch, in order of size, until the budget is used; returns
+    [(index, u levels, leaf masks)], seconds, DoF."""
     from oracle.lgf import LGF
-    t0 = time.perf_counter()
-    op = FLGF(LGF(), prob.coords[0], prob.N, 6)
-    for k in range(op.tree.top + 1):
-        for d in np.ndindex(7, 7, 7):
-            op.kernel_spectrum(k, np.array(d) - 3)
-    setup = time.perf_counter() - t0
-    rng = np.random.default_rng(seed)
-    nz = np.nonzero(np.any(prob.f[0] != 0, axis=(1, 2, 3)))[0]
-    targets = np.sort(rng.choice(nz, size=min(n_sample, nz.size), replace=False))
-    t1 = time.perf_counter()
-    u = op.apply(prob.f[0], h=prob.h0, targets=targets)
-    dt = time.perf_counter() - t1
-    return targets, u[targets], dt, setup, op
+    from oracle.multires import multires_solve
+    G = LGF()
+    order = sorted(range(len(probs)), key=lambda i: sum(len(c) for c in probs[i].coords))
+    out, t_used, dof = [], 0.0, 0
+    for i in order:
+        p = probs[i]
+        t = time.perf_counter()
+        u, leaf = multires_solve(G, p.coords, p.f, p.N, 6, p.h0)
+        t_used += time.perf_counter() - t
+        out.append((i, u, leaf))
+        dof += p.dof()
+        if t_used >= budget_s:
+            break
+    return out, t_used, dof
 
 
 def run_reference(a, rank, world):
-    """The oracle arm: FP64 CPU oracle on bounded samples of the workload."""
+    """The oracle arm: the FP64 CPU oracle on bounded samples of the batched workload."""
     if rank != 0:
         return
-    from paper_1911_10228_gb300.inputs import config_uniform_256
-    prob = config_uniform_256()
-    from oracle.flgf import FLGF
     from oracle.lgf import LGF
-    op = FLGF(LGF(), prob.coords[0], prob.N, 6)
-    for k in range(op.tree.top + 1):
-        for d in np.ndindex(7, 7, 7):
-            op.kernel_spectrum(k, np.array(d) - 3)
-    rng = np.random.default_rng(1)
-    nz = np.nonzero(np.any(prob.f[0] != 0, axis=(1, 2, 3)))[0]
-    per_step = 2
-    times = []
-    for i in range(a.warmup + a.steps):
-        tg = np.sort(rng.choice(nz, per_step, replace=False))
+    from oracle.multires import multires_solve
+    from paper_1911_10228_gb300.inputs import config_batched
+    probs = config_batched(a.problems)
+    order = sorted(range(len(probs)), key=lambda i: sum(len(c) for c in probs[i].coords))
+    G = LGF()
+    times, dofs = [], []
+    for s in range(a.warmup + a.steps):
+        p = probs[order[s % 2]]           # the two smallest problems in turn, so the run stays within minutes
         t = time.perf_counter()
-        op.apply(prob.f[0], h=prob.h0, targets=tg)
-        if i >= a.warmup:
+        multires_solve(G, p.coords, p.f, p.N, 6, p.h0)
+        if s >= a.warmup:
             times.append(time.perf_counter() - t)
+            dofs.append(p.dof())
+    value = float(np.sum(dofs) / np.sum(times))
     ms = 1e3 * float(np.mean(times))
-    dof = per_step * prob.N ** 3
-    value = dof / (ms / 1e3)
-    cores = os.cpu_count()
-    sample = f"{per_step} of 4096 target blocks per step (full upward and downward passes, all levels)"
+    sample = (f"one of the 2 smallest of the {len(probs)} problems per step, in turn (full multi-resolution "
+              f"solve), {np.mean(dofs):.0f} DoF per step on average")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": 16, "n_interp": 6, "blocks": 4096, "dof": prob.dof(),
-                   "parallelism": "oracle on host cores"},
-        "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "config": {"workload": BATCH_WORKLOAD, "problems": len(probs), "parallelism": "oracle on host cores"},
+        "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
-def run_ours(a, rank, world, dist):
+def run_ours(a, rank, world):
     import torch
 
     from paper_1911_10228_gb300 import flgf as F
     from paper_1911_10228_gb300 import multirank as MR
-    from paper_1911_10228_gb300.inputs import config_uniform_256
+    from paper_1911_10228_gb300.inputs import config_batched
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    prob = config_uniform_256()
-    N = prob.N
-    dof = prob.dof()
-    f64 = torch.as_tensor(prob.f[0])
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    hbm, hbm_src, sm_mhz_peak = peaks()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    res = {}
-    sampler = ClockSampler(dev)  # covers the timed regions of every precision
+    sampler = ClockSampler(dev)
+    legs = set(x for x in a.legs.split(",") if x)
     precs = [p for p in a.precisions.split(",") if p]
     if "fp32" not in precs:
         raise SystemExit("the headline value is the FP32 form: --precisions must include fp32")
-    for prec in precs:
-        ctx = F.Context(N=N, n_interp=6, precision=prec)
-        bs = F.BlockSet(ctx, [prob.coords], [prob.h0])
-        bs.load_source(0, 0, f64.to("cuda"))
-        for _ in range(a.warmup):
-            bs.solve()
-        torch.cuda.synchronize()
-        bs.set_option(F.OPT_TIMING, 1)
-        bs.stage_times(reset=True)
-        steps = a.steps if prec == "fp32" else max(3, min(a.steps, 10))
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+
+    def timed(stream, fn, n):
+        """ms per call of fn over n calls (CUDA events on the library stream,
+        L2 flushed before each), max over ranks."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
         MR.barrier("cuda")
         torch.cuda.synchronize()
         sampler.start()
-        for s0, s1 in evs:
-            with torch.cuda.stream(ctx.stream):
+        for s0, s1 in ev:
+            with torch.cuda.stream(stream):
                 flush.zero_()
-            s0.record(ctx.stream)
-            bs.solve()
-            s1.record(ctx.stream)
+            s0.record(stream)
+            fn()
+            s1.record(stream)
         torch.cuda.synchronize()
         sampler.stop()
         MR.barrier("cuda")
-        step_ms = [s0.elapsed_time(s1) for s0, s1 in evs]
-        total = MR.all_max(sum(step_ms), "cuda")   # the slowest rank's time
-        stage, n_timed = bs.stage_times(reset=True)
-        bs.set_option(F.OPT_TIMING, 0)
-        res[prec] = {
-            "ms_per_step": total / steps, "steps": steps, "launches": bs.launch_count(),
-            "stages_ms": {k: v / max(n_timed, 1) for k, v in stage.items()},
-            "work": bs.work_counts(), "ctx": ctx, "bs": bs,
-        }
-        res[prec]["u"] = bs.potential(0, 0).double().cpu().numpy()
+        return MR.all_max(float(np.mean([s0.elapsed_time(s1) for s0, s1 in ev])), "cuda")
 
-    # batched form: 64 independent refined problems in one block set, every stage
-    # of all problems in the same launches, the whole solve replayed as a CUDA graph
-    batched = None
-    if not a.no_batched:
-        from paper_1911_10228_gb300.inputs import config_batched
-        # each rank solves its own 64 problems (seeds 64 r .. 64 r + 63): no exchange between ranks
-        seeds = MR.problem_seeds(64, rank)
-        probs = config_batched(64, first_seed=seeds[0])
-        bdof_rank = sum(p.dof() for p in probs)
-        bdof = MR.all_sum(bdof_rank, "cuda")
-        batched = {"workload": "64 random sparse problems per GPU (seeds 64 r .. 64 r + 63 on rank r), 16^3 blocks, "
-                               "block counts log-uniform in [8, 4096] over 1-3 levels, 1-4 Gaussians each, one block "
-                               "set, CUDA graph",
-                   "dof": int(bdof), "dof_rank0": bdof_rank,
-                   "blocks_rank0": int(sum(len(c) for p in probs for c in p.coords))}
-        outs = {}
-        plan = None
-        for prec in precs:
-            bctx = F.Context(N=16, n_interp=6, precision=prec)
-            if plan is None and a.plan:
-                pct, tile = a.plan.split("/")
-                plan = (int(pct), tuple(int(v) for v in tile.split("x")))
-                batched["plan"] = {"list_pct": plan[0], "tile": list(plan[1]), "source": "--plan"}
-            if plan is None:
-                # pick the MAC plan (dense tile, pair-list threshold) on this mesh
-                from paper_1911_10228_gb300.autotune import autotune
-                t0 = time.time()
-                plan, table = autotune(bctx, [p.coords for p in probs], [p.h0 for p in probs], reps=2)
-                batched["autotune"] = {"precision": prec, "plan": {"list_pct": plan[0], "tile": list(plan[1])},
-                                       "seconds": round(time.time() - t0, 1),
-                                       "ms_per_solve": {f"{k[0]}/{'x'.join(map(str, k[1]))}": round(v, 2)
-                                                        for k, v in table.items()}}
-            bctx.set_plan(list_pct=plan[0], tile=plan[1])
-            bbs = F.BlockSet(bctx, [p.coords for p in probs], [p.h0 for p in probs])
-            for i, p in enumerate(probs):
-                for l, f in enumerate(p.f):
-                    bbs.load_source(i, l, torch.as_tensor(f))
-            bbs.set_option(F.OPT_GRAPH, 1)
-            # the FP64 batched solve takes seconds: one warm-up and one step (it serves the error check)
-            for _ in range(max(1, a.warmup) if prec == "fp32" else 1):
-                bbs.solve()
-            torch.cuda.synchronize()
-            nb = a.steps if prec == "fp32" else 1
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb)]
-            MR.barrier("cuda")
-            torch.cuda.synchronize()
-            sampler.start()
-            for s0, s1 in ev:
-                with torch.cuda.stream(bctx.stream):
-                    flush.zero_()
-                s0.record(bctx.stream)
-                bbs.solve()
-                s1.record(bctx.stream)
-            torch.cuda.synchronize()
-            sampler.stop()
-            MR.barrier("cuda")
-            ms = MR.all_max(float(np.mean([s0.elapsed_time(s1) for s0, s1 in ev])), "cuda")
-            batched[prec] = {"value": bdof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "steps": nb,
-                             "launches_per_step": bbs.launch_count()}
-            outs[prec] = [[bbs.potential(i, l) for l in range(p.n_levels)] for i, p in enumerate(probs)]
+    def fp32_alu_peak():
+        return n_sm * FP32_LANES * 2 * sm_mhz_peak * 1e6 / 1e12
+
+    # ------------------------------------------------------------------ batched
+    seeds = MR.problem_seeds(a.problems, rank)
+    probs = config_batched(a.problems, first_seed=seeds[0])
+    bdof_rank = sum(p.dof() for p in probs)
+    bdof = MR.all_sum(bdof_rank, "cuda")
+    batched = {"problems": len(probs), "blocks_rank0": int(sum(len(c) for p in probs for c in p.coords)),
+               "dof": int(bdof), "dof_rank0": int(bdof_rank)}
+    plan = None
+    if a.plan:
+        pct, tile = a.plan.split("/")
+        plan = (int(pct), tuple(int(v) for v in tile.split("x")))
+        batched["plan"] = {"list_pct": plan[0], "tile": list(plan[1]), "source": "--plan"}
+    outs, res = {}, {}
+    for prec in precs:
+        bctx = F.Context(N=16, n_interp=6, precision=prec)
+        if plan is None:
+            from paper_1911_10228_gb300.autotune import autotune
+            t0 = time.time()
+            plan, table = autotune(bctx, [p.coords for p in probs], [p.h0 for p in probs], reps=2)
+            batched["plan"] = {"list_pct": plan[0], "tile": list(plan[1]), "source": "autotune",
+                               "seconds": round(time.time() - t0, 1),
+                               "ms_per_solve": {f"{k[0]}/{'x'.join(map(str, k[1]))}": round(v, 2)
+                                                for k, v in table.items()}}
+        bctx.set_plan(list_pct=plan[0], tile=plan[1])
+        bbs = F.BlockSet(bctx, [p.coords for p in probs], [p.h0 for p in probs])
+        for i, p in enumerate(probs):
+            for l, f in enumerate(p.f):
+                bbs.load_source(i, l, torch.as_tensor(f))
+        bbs.set_option(F.OPT_GRAPH, 1)
+        bbs.set_option(F.OPT_TIMING, 1)    # stage events inside the captured graph
+        # the FP64 batched solve takes seconds: one warm-up and one step (it also serves the error check)
+        for _ in range(max(1, a.warmup) if prec == "fp32" else 1):
+            bbs.solve()
+        torch.cuda.synchronize()
+        bbs.stage_times(reset=True)
+        nb = a.steps if prec == "fp32" else 1
+        ms = timed(bctx.stream, bbs.solve, nb)
+        stage, n_timed = bbs.stage_times(reset=True)
+        res[prec] = {"value": bdof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "steps": nb,
+                     "launches_per_step": bbs.launch_count(),
+                     "stages_ms": {k: v / max(n_timed, 1) for k, v in stage.items()},
+                     "work": bbs.work_counts()}
+        outs[prec] = [[bbs.potential(i, l) for l in range(p.n_levels)] for i, p in enumerate(probs)]
+        if prec == "fp32":
+            keep_ctx, keep_bs = bctx, bbs
+        else:
             bbs.close()
             bctx.close()
-        if "fp64" in outs:   # FP32 batched form against the FP64 solve, leaf cells, max over all problems
-            num, den = 0.0, 0.0
-            for u32s, u64s, p in zip(outs["fp32"], outs["fp64"], probs):
-                for x32, x64, lm in zip(u32s, u64s, p.leaf_masks()):
-                    m = torch.as_tensor(lm, device=x64.device)
-                    num = max(num, float((x32.double() - x64)[m].abs().max()))
-                    den = max(den, float(x64[m].abs().max()))
-            batched["fp32_vs_fp64_linf"] = num / den
-        del outs
+    if "fp64" in outs:
+        batched["fp32_vs_fp64_linf"] = leaf_linf(outs["fp32"], outs["fp64"], probs)
+    N = 16
+    NW = 2 * N * 2 * N * (N + 1)
+    r32 = res["fp32"]
+    mac_ms = r32["stages_ms"]["spectrum_mac"]
+    mac_flops = r32["work"]["pairs"] * NW * 8.0
+    mac_tflops = mac_flops / (mac_ms / 1e3) / 1e12 if mac_ms > 0 else None
+    batched["fp32"] = {k: v for k, v in r32.items() if k != "work"}
+    batched["fp32"]["pairs"] = r32["work"]["pairs"]
+    if "fp64" in res:
+        r64 = res["fp64"]
+        batched["fp64"] = {k: v for k, v in r64.items() if k != "work"}
+        batched["fp32_over_fp64"] = r32["value"] / r64["value"]
 
-    # refined meshes: the 3-level torus (FP32 and FP64, graph-replayed) and the
-    # adjoint (gradient) solve on the linked tori, FP32
-    multires, adjoint = None, None
-    if not a.no_multires:
-        from paper_1911_10228_gb300.inputs import config_linked_tori, config_torus_128
-
-        def timed(stream, fn, n):
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
-            MR.barrier("cuda")
+    # ------------------------------------------------------------------ uniform 256^3
+    uniform = None
+    if "uniform" in legs:
+        from paper_1911_10228_gb300.inputs import config_uniform_256
+        up = config_uniform_256()
+        udof = up.dof()
+        f64 = torch.as_tensor(up.f[0])
+        uniform = {"workload": UNIFORM_WORKLOAD, "dof": udof}
+        for prec in precs:
+            ctx = F.Context(N=16, n_interp=6, precision=prec)
+            bs = F.BlockSet(ctx, [up.coords], [up.h0])
+            bs.load_source(0, 0, f64.to("cuda"))
+            bs.set_option(F.OPT_TIMING, 1)
+            for _ in range(a.warmup):
+                bs.solve()
             torch.cuda.synchronize()
-            sampler.start()
-            for s0, s1 in ev:
-                with torch.cuda.stream(stream):
-                    flush.zero_()
-                s0.record(stream)
-                fn()
-                s1.record(stream)
-            torch.cuda.synchronize()
-            sampler.stop()
-            MR.barrier("cuda")
-            return MR.all_max(float(np.mean([s0.elapsed_time(s1) for s0, s1 in ev])), "cuda")
+            bs.stage_times(reset=True)
+            n = a.steps if prec == "fp32" else max(3, min(a.steps, 10))
+            ms = timed(ctx.stream, bs.solve, n)
+            stage, nt = bs.stage_times(reset=True)
+            st = {k: v / max(nt, 1) for k, v in stage.items()}
+            w = bs.work_counts()
+            rs = 4 if prec == "fp32" else 8
+            flops = w["pairs"] * NW * 8.0
+            row = {"value": udof * world / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "steps": n,
+                   "stages_ms": st, "launches_per_step": bs.launch_count(),
+                   "spectrum_mac_tflops": flops / (st["spectrum_mac"] / 1e3) / 1e12,
+                   "fft_forward_gbs": w["fwd_ffts"] * (N ** 3 * rs + NW * 2 * rs) / (st["fft_forward"] / 1e3) / 1e9,
+                   "fft_inverse_gbs": w["inv_ffts"] * (N ** 3 * rs + NW * 2 * rs) / (st["fft_inverse"] / 1e3) / 1e9}
+            if prec == "fp32":
+                row["spectrum_mac_frac_of_fp32_fma"] = row["spectrum_mac_tflops"] / fp32_alu_peak()
+                row["fft_forward_frac_of_hbm"] = row["fft_forward_gbs"] / hbm
+                row["fft_inverse_frac_of_hbm"] = row["fft_inverse_gbs"] / hbm
+            else:
+                row["spectrum_mac_frac_of_fp64_nominal"] = row["spectrum_mac_tflops"] / FP64_NOMINAL_TFLOPS
+            uniform[prec] = row
+            uniform.setdefault("_u", {})[prec] = bs.potential(0, 0).double().cpu().numpy()
+            bs.close()
+            ctx.close()
 
+    # ------------------------------------------------------------------ refined torus
+    multires = None
+    if "multires" in legs:
+        from paper_1911_10228_gb300.inputs import config_torus_128
         tp = config_torus_128()
         tdof = tp.dof()
         multires = {"workload": "Gaussian-core torus (R 0.25, sigma 0.03), base 128^3 in 8^3 blocks of 16^3, 3 levels "
                                 "refined where |f| > 1e-3 max, n_I=6, source correction on, CUDA graph",
                     "dof": tdof, "blocks": int(sum(len(c) for c in tp.coords))}
-        outs = {}
-        for prec in precs:
+        touts = {}
+        for prec, comp in ([("fp32", 1), ("fp32", 0)] + ([("fp64", 0)] if "fp64" in precs else [])):
             mctx = F.Context(N=16, n_interp=6, precision=prec)
             mbs = F.BlockSet(mctx, [tp.coords], [tp.h0])
+            if prec == "fp32":
+                mbs.set_option(F.OPT_COMPENSATED, comp)
             for l, f in enumerate(tp.f):
                 mbs.load_source(0, l, torch.as_tensor(f))
             mbs.set_option(F.OPT_GRAPH, 1)
@@ -365,18 +390,22 @@ def run_ours(a, rank, world, dist):
                 mbs.solve()
             n = a.steps if prec == "fp32" else 2
             ms = timed(mctx.stream, mbs.solve, n)
-            multires[prec] = {"value": tdof * world / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "steps": n,
-                              "launches_per_step": mbs.launch_count()}
-            outs[prec] = [mbs.potential(0, l) for l in range(tp.n_levels)]
+            key = prec if prec == "fp64" else ("fp32" if comp else "fp32_uncompensated")
+            multires[key] = {"value": tdof * world / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "steps": n,
+                             "launches_per_step": mbs.launch_count()}
+            touts[key] = [mbs.potential(0, l) for l in range(tp.n_levels)]
             mbs.close()
             mctx.close()
-        if "fp64" in outs:
-            lm = tp.leaf_masks()
-            num = max(float((x.double() - y)[torch.as_tensor(m, device=y.device)].abs().max())
-                      for x, y, m in zip(outs["fp32"], outs["fp64"], lm))
-            den = max(float(y[torch.as_tensor(m, device=y.device)].abs().max()) for y, m in zip(outs["fp64"], lm))
-            multires["fp32_vs_fp64_linf"] = num / den
-        del outs
+        if "fp64" in touts:
+            multires["fp32_vs_fp64_linf"] = leaf_linf([touts["fp32"]], [touts["fp64"]], [tp])
+            multires["fp32_uncompensated_vs_fp64_linf"] = leaf_linf([touts["fp32_uncompensated"]], [touts["fp64"]],
+                                                                    [tp])
+        del touts
+
+    # ------------------------------------------------------------------ adjoint
+    adjoint = None
+    if "adjoint" in legs:
+        from paper_1911_10228_gb300.inputs import config_linked_tori
         lt = config_linked_tori()
         ldof = lt.dof()
         actx = F.Context(N=16, n_interp=6, precision="fp32")
@@ -397,127 +426,126 @@ def run_ours(a, rank, world, dist):
         abs_.close()
         actx.close()
 
-    # end-to-end FP32 through the public API with pinned host buffers
-    r32 = res["fp32"]
-    bs = r32["bs"]
-    ctx = r32["ctx"]
-    h_src = torch.empty(tuple(f64.shape), dtype=torch.float32, pin_memory=True)
-    h_src.copy_(f64.float())
-    h_out = torch.empty_like(h_src, pin_memory=True)
-    # Pipelined as a time-stepping caller would run it: the next step's source
-    # is loaded (host to device, on the library's copy stream) while the
-    # current solve runs, then the current potential is read back (device to
-    # host) and the next solve is enqueued.  Every step still moves its whole
-    # input in and its whole result out; the wall time covers them all.
-    def e2e_run(n):
-        bs.load_source(0, 0, h_src)
-        bs.solve()
-        for i in range(n):
-            if i + 1 < n:
-                bs.load_source(0, 0, h_src)
-            bs.potential_host(0, 0, out=h_out.numpy())
-            if i + 1 < n:
-                bs.solve()
-
-    e2e_ms = []
+    # ------------------------------------------------------------------ end to end (batched, host buffers)
+    e2e = None
     if not a.no_e2e:
-        e2e_run(a.warmup)
+        keys = [(i, l) for i, p in enumerate(probs) for l in range(p.n_levels)]
+        h_src = {k: torch.empty(tuple(probs[k[0]].f[k[1]].shape), dtype=torch.float32, pin_memory=True) for k in keys}
+        for (i, l), t in h_src.items():
+            t.copy_(torch.as_tensor(probs[i].f[l]).float())
+        h_out = {k: torch.empty_like(t, pin_memory=True) for k, t in h_src.items()}
+        nbytes = sum(t.numel() * 4 for t in h_src.values())
+
+        # As a time-stepping caller runs it: the next step's sources are loaded
+        # (host to device, on the library's copy stream) while the current solve
+        # runs, then the current potentials are read back and the next solve is
+        # enqueued.  Every step moves all inputs in and all results out.
+        def load_all():
+            for (i, l), t in h_src.items():
+                keep_bs.load_source(i, l, t)
+
+        def read_all():
+            for (i, l), t in h_out.items():
+                keep_bs.potential_host(i, l, out=t.numpy())
+
+        def e2e_run(n):
+            load_all()
+            keep_bs.solve()
+            for s in range(n):
+                if s + 1 < n:
+                    load_all()
+                read_all()
+                if s + 1 < n:
+                    keep_bs.solve()
+
+        keep_bs.set_option(F.OPT_TIMING, 0)
+        e2e_run(max(1, a.warmup))
         MR.barrier("cuda")
         t = time.perf_counter()
         e2e_run(a.steps)
-        e2e_ms.append(1e3 * (time.perf_counter() - t))
-    e2e = MR.all_max(sum(e2e_ms), "cuda")
-    e2e_ms_step = e2e / a.steps if e2e_ms else None
-    nbytes = h_src.numel() * 4
+        e2e_ms = MR.all_max(1e3 * (time.perf_counter() - t), "cuda") / a.steps
+        e2e = {"value": bdof / (e2e_ms / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms,
+               "note": "pinned host buffers through the C ABI (flgf_load_source / flgf_get_potential with host "
+                       "pointers); the next step's loads overlap the current solve"}
 
-    # accuracy and CPU baseline against the FP64 oracle (rank 0, one GPU only)
-    acc, cpu = None, None
+    # ------------------------------------------------------------------ CPU oracle baseline and errors
+    cpu, err = None, None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        targets, u_ref, dt, setup, _ = oracle_sample(prob, a.cpu_sample)
-        def errs(u):
-            d = u[targets] - u_ref
-            return {"linf": float(np.max(np.abs(d)) / np.max(np.abs(u_ref))),
-                    "l2": float(np.linalg.norm(d) / np.linalg.norm(u_ref))}
-        acc = {p + "_vs_oracle": errs(res[p]["u"]) for p in res}
-        acc.update({
-               "sample": f"{len(targets)} of 4096 target blocks (seeded), FP64 oracle"})
-        cpu = {"value": len(targets) * N ** 3 / dt, "unit": "DoF/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{len(targets)} of 4096 target blocks with full upward/downward passes; "
-                         f"{dt:.1f} s solve, {setup:.1f} s LGF/kernel-spectrum setup excluded"}
+        sample, secs, sdof = oracle_batch_sample(probs, a.cpu_seconds)
+        err = {"sample": f"{len(sample)} smallest of the {len(probs)} problems, FP64 oracle (full multi-resolution "
+                         f"solve), leaf cells"}
+        for prec in outs:
+            worst = 0.0
+            for i, u, leaf in sample:
+                scale = max(np.max(np.abs(x[m])) for x, m in zip(u, leaf) if m.any())
+                for l in range(probs[i].n_levels):
+                    if leaf[l].any():
+                        g = outs[prec][i][l].double().cpu().numpy()
+                        worst = max(worst, float(np.max(np.abs(g[leaf[l]] - u[l][leaf[l]])) / scale))
+            err[prec + "_vs_oracle_linf"] = worst
+        cpu = {"value": sdof / secs, "unit": "DoF/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{len(sample)} smallest of the {len(probs)} problems of the batched workload "
+                         f"({sdof} DoF), full multi-resolution solve, {secs:.1f} s"}
+        if uniform is not None:
+            # the 256^3 leg against the oracle on 8 sampled target blocks
+            from oracle.flgf import FLGF
+            from oracle.lgf import LGF
+            from paper_1911_10228_gb300.inputs import config_uniform_256
+            up = config_uniform_256()
+            op = FLGF(LGF(), up.coords[0], up.N, 6)
+            nz = np.nonzero(np.any(up.f[0] != 0, axis=(1, 2, 3)))[0]
+            tg = np.sort(np.random.default_rng(0).choice(nz, 8, replace=False))
+            ref = op.apply(up.f[0], h=up.h0, targets=tg)[tg]
+            for prec, u in uniform["_u"].items():
+                d = u[tg] - ref
+                uniform[prec]["vs_oracle_linf"] = float(np.max(np.abs(d)) / np.max(np.abs(ref)))
+                uniform[prec]["vs_oracle_l2"] = float(np.linalg.norm(d) / np.linalg.norm(ref))
+            uniform["oracle_sample"] = "8 of 4096 target blocks (seeded), FP64 oracle"
+    if uniform is not None:
+        uniform.pop("_u", None)
 
-    hbm, hbm_src = peaks()
-    NW = 2 * N * 2 * N * (N + 1)
-    rows = {}
-    for prec, rs in (("fp32", 4), ("fp64", 8)):
-        if prec not in res:
-            continue
-        r = res[prec]
-        w = r["work"]
-        mac_ms = r["stages_ms"]["spectrum_mac"]
-        flops = w["pairs"] * NW * 8.0
-        fwd_bytes = w["fwd_ffts"] * (N ** 3 * rs + NW * 2 * rs)
-        inv_bytes = w["inv_ffts"] * (N ** 3 * rs + NW * 2 * rs)
-        rows[prec] = {
-            "mac_tflops": flops / (mac_ms / 1e3) / 1e12 if mac_ms > 0 else None,
-            "fft_fwd_gbs": fwd_bytes / (r["stages_ms"]["fft_forward"] / 1e3) / 1e9,
-            "fft_inv_gbs": inv_bytes / (r["stages_ms"]["fft_inverse"] / 1e3) / 1e9,
-            "mac_flops": flops,
-        }
-    ach = rows["fp32"]["mac_tflops"]
+    peak = fp32_alu_peak()
     line = {
         "metric": METRIC,
-        "value": dof * world / (res["fp32"]["ms_per_step"] / 1e3),
+        "value": r32["value"],
         "unit": "DoF/s",
         "n_gpus": world,
         "steps": a.steps,
         "warmup": a.warmup,
-        "ms_per_step": res["fp32"]["ms_per_step"],
+        "ms_per_step": r32["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "n_interp": 6, "blocks": 4096, "dof": dof,
-                   "l2": "flushed before every timed step (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "rel_err": acc,
-        "fp64_plain": None if "fp64" not in res else {
-            "value": dof * world / (res["fp64"]["ms_per_step"] / 1e3), "unit": "DoF/s",
-            "ms_per_step": res["fp64"]["ms_per_step"], "steps": res["fp64"]["steps"],
-            "stages_ms": res["fp64"]["stages_ms"],
-            "spectrum_mac_tflops": rows["fp64"]["mac_tflops"],
-            "spectrum_mac_frac_of_fp64_nominal": (rows["fp64"]["mac_tflops"] or 0) / FP64_NOMINAL_TFLOPS,
-            "spectrum_mac_note": "algorithmic 8 flop per complex multiply-add; the FP64 kernel issues 3 FMAs "
-                                 "(6 flop) per pair in the three-product form, so 1.0 of nominal means the FP64 "
-                                 "pipe runs at 75 %"},
-        "roofline": {"bound": "alu", "kernel": "hadamard_kernel<float,2> (spectrum MAC, a3)",
-                     "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": (ach / FP32_ALU_PEAK_TFLOPS) if ach else None,
-                     "traffic": ncu_traffic("hadamard.cu", "hadamard_kernel"),
-                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
-                     "flops_per_launch": rows["fp32"]["mac_flops"]},
-        "hbm_kernels": {"peak_gbs": hbm, "peak_source": hbm_src,
-                        "fft_forward_gbs": rows["fp32"]["fft_fwd_gbs"],
-                        "fft_forward_frac": rows["fp32"]["fft_fwd_gbs"] / hbm,
-                        "fft_inverse_gbs": rows["fp32"]["fft_inv_gbs"],
-                        "fft_inverse_frac": rows["fp32"]["fft_inv_gbs"] / hbm},
-        "stages_ms": res["fp32"]["stages_ms"],
+        "config": {"workload": BATCH_WORKLOAD, "problems": len(probs), "N": 16, "n_interp": 6,
+                   "dof": int(bdof), "l2": "flushed before every timed step (256 MB write)",
+                   "compensated_coarse_levels": True,
+                   "parallelism": "independent problems per rank" if world > 1 else "single GPU"},
+        "rel_err": {"fp32_vs_fp64_linf": batched.get("fp32_vs_fp64_linf"), **(err or {})},
+        "roofline": {"bound": "alu", "kernel": "spectrum MAC (hadamard_kernel + hadamard_list_kernel), "
+                                               "all launches of one batched solve",
+                     "achieved": mac_tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (mac_tflops / peak) if mac_tflops else None,
+                     "traffic": ncu_traffic("hadamard.cu", "hadamard", f"batched{a.problems}"),
+                     "peak_note": f"FP32 FMA: {n_sm} SMs x {FP32_LANES} lanes x 2 flop x {sm_mhz_peak:.0f} MHz",
+                     "flops_per_step": mac_flops,
+                     "flops_note": "useful (target, source) block pairs x 2N*2N*(N+1) frequencies x 8 flop"},
+        "hbm": {"peak_gbs": hbm, "peak_source": hbm_src},
         "batched": batched,
+        "uniform256": uniform,
         "multires": multires,
         "adjoint": adjoint,
         "cpu_baseline": cpu,
-        "e2e": None if e2e_ms_step is None else {
-            "value": dof * world / (e2e_ms_step / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms_step,
-            "note": "pinned host buffers; the next step's source load overlaps the current solve"},
-        "gpu_launches": res["fp32"]["launches"] * a.steps,
+        "e2e": e2e,
+        "gpu_launches": r32["launches_per_step"] * a.steps,
         "clocks": sampler.summary(),
     }
     if rank == 0:
         print(json.dumps(line))
-    for prec in res:
-        res[prec]["bs"].close()
-        res[prec]["ctx"].close()
+    keep_bs.close()
+    keep_ctx.close()
 
 
 def main():
@@ -532,7 +560,7 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
-    run_ours(a, rank, world, dist)
+    run_ours(a, rank, world)
     if dist:
         import torch
         torch.distributed.destroy_process_group()
