@@ -16,8 +16,9 @@ of problems, against the FP64 CPU oracle.
 
 Further legs (keys of the JSON line): the 256^3 uniform lattice (16^3 blocks,
 n_I = 6), the 3-level torus with the FP32 compensation off and on, the
-adjoint solve on the linked tori, and the end-to-end batched solve through the
-C ABI with host buffers.
+adjoint solve on the linked tori, the three-component vortex ring as one
+vector block set beside one scalar component, and the end-to-end batched solve
+through the C ABI with host buffers.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -60,7 +61,7 @@ def args_parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--problems", type=int, default=64, help="problems of the batched workload per GPU")
-    ap.add_argument("--legs", default="batched,uniform,multires,adjoint",
+    ap.add_argument("--legs", default="batched,uniform,multires,adjoint,vector",
                     help="legs to run; the batched leg (the headline) always runs")
     ap.add_argument("--precisions", default="fp32,fp64", help="contexts to time (profiling runs use fp32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -426,6 +427,41 @@ def run_ours(a, rank, world):
         abs_.close()
         actx.close()
 
+    # ------------------------------------------------------------------ vector (three components, one mesh)
+    vector = None
+    if "vector" in legs:
+        from paper_1911_10228_gb300.inputs import cell_centres, config_vortex_ring, vortex_ring_vector
+        vp, _ = config_vortex_ring(3, 16, 8)
+        comps = [[], [], []]
+        for l, c in enumerate(vp.coords):
+            _, w = vortex_ring_vector(cell_centres(c, 16, vp.h0 / (1 << l)))
+            for k in range(3):
+                comps[k].append(torch.as_tensor(np.ascontiguousarray(w[..., k]).astype(np.float32)))
+        vector = {"workload": "vortex ring (Sec. 3.1: c1 1e3, c2 10, R 0.125), base 128^3 in 8^3 blocks of 16^3, "
+                              "3 levels, the three vorticity components as one vector block set, FP32, CUDA graph",
+                  "dof_per_component": vp.dof(), "blocks": int(sum(len(c) for c in vp.coords))}
+        vctx = F.Context(N=16, n_interp=6, precision="fp32")
+        for key, nc in (("vector3", 3), ("scalar1", 1)):
+            vbs = F.BlockSet(vctx, [vp.coords] * nc, [vp.h0] * nc, vector=nc > 1)
+            for k in range(nc):
+                for l in range(vp.n_levels):
+                    vbs.load_source(k, l, comps[k][l])
+            vbs.set_option(F.OPT_GRAPH, 1)
+            vbs.set_option(F.OPT_TIMING, 1)
+            for _ in range(max(1, a.warmup)):
+                vbs.solve()
+            torch.cuda.synchronize()
+            vbs.stage_times(reset=True)
+            n = min(a.steps, 10)
+            ms = timed(vctx.stream, vbs.solve, n)
+            stage, nt = vbs.stage_times(reset=True)
+            vector[key] = {"ms_per_step": ms, "steps": n, "spectrum_mac_ms": stage["spectrum_mac"] / max(nt, 1),
+                           "value": nc * vp.dof() * world / (ms / 1e3), "unit": "DoF/s (all components)"}
+            vbs.close()
+        vctx.close()
+        vector["mac_ms_over_3_scalar"] = vector["vector3"]["spectrum_mac_ms"] / (3 * vector["scalar1"]["spectrum_mac_ms"])
+        vector["solve_ms_over_3_scalar"] = vector["vector3"]["ms_per_step"] / (3 * vector["scalar1"]["ms_per_step"])
+
     # ------------------------------------------------------------------ end to end (batched, host buffers)
     e2e = None
     if not a.no_e2e:
@@ -537,6 +573,7 @@ def run_ours(a, rank, world):
         "uniform256": uniform,
         "multires": multires,
         "adjoint": adjoint,
+        "vector": vector,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": r32["launches_per_step"] * a.steps,

@@ -103,6 +103,13 @@ void flgf_destroy(flgf_ctx* ctx);
  *                      Tiles are the unit of the pair-list decision, and
  *                      their order is the order in which parents are packed
  *                      into the dense kernel's groups.
+ *   FLGF_CTX_MAC       FP32 contexts: 1 (default) runs the spectrum MAC with one
+ *                      frequency per thread and one target parent per warp
+ *                      (absent cells and children are skipped warp-uniformly;
+ *                      FLGF_CTX_LIST_PCT and FLGF_CTX_ORDER do not apply);
+ *                      0 runs the parent-group kernel (one parent per thread)
+ *                      and the pair-list kernel.  FP64 contexts always use the
+ *                      latter.
  *   FLGF_CTX_ORDER     0 (default): the parents of each dense-kernel group keep
  *                      the tile order; 1: they are ordered by their set of
  *                      neighbours with sources (most first, equal sets
@@ -116,7 +123,7 @@ void flgf_destroy(flgf_ctx* ctx);
  *                      and the adjoint's first use allocate) reports
  *                      FLGF_ENOMEM without allocating; 0 disarms.  One shot.
  * FLGF_EINVAL for an unknown key or a value out of range. */
-enum { FLGF_CTX_LIST_PCT = 1, FLGF_CTX_TILE = 2, FLGF_CTX_FAIL_ALLOC = 3, FLGF_CTX_ORDER = 4 };
+enum { FLGF_CTX_LIST_PCT = 1, FLGF_CTX_TILE = 2, FLGF_CTX_FAIL_ALLOC = 3, FLGF_CTX_ORDER = 4, FLGF_CTX_MAC = 5 };
 int flgf_ctx_set_option(flgf_ctx* ctx, int key, int value);
 
 /* Message of the last failure on this context (never NULL; "" if none). */
@@ -164,6 +171,20 @@ int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, con
 int flgf_blockset_create_masked(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
                                 const int32_t* coords, const double* h0, const uint8_t* want,
                                 flgf_blockset** out);
+/* A vector Poisson problem (Sec. 3.1: the Cartesian components of the
+ * streamfunction of a vorticity field, each a scalar problem on the same
+ * mesh): n_components copies of one mesh (n_levels, nblk[n_levels], coords as
+ * for one problem of flgf_blockset_create) as the problems 0 .. n_components-1
+ * of one block set, problem c holding component c.  An FP32 block set of
+ * three components (FLGF_CTX_MAC = 1) runs the dense spectrum products of
+ * all components in one kernel in which each kernel-spectrum read serves the
+ * three components' products; the sums are the same, in the same order, as
+ * in three independent solves, so each component's potential equals its own
+ * scalar solve bit for bit.  Other precisions and component counts solve the
+ * components as independent problems of the block set.  1 <= n_components
+ * <= 64; arrays are borrowed for the call. */
+int flgf_blockset_create_vector(flgf_ctx* ctx, int n_components, int n_levels, const int* nblk,
+                                const int32_t* coords, double h0, flgf_blockset** out);
 void flgf_blockset_destroy(flgf_blockset* bs);
 
 /* Total leaf cells (degrees of freedom of the composite mesh) over all problems. */

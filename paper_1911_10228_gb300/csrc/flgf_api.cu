@@ -24,6 +24,7 @@ struct flgf_ctx {
   int list_pct = 30;             // pair-list MAC below this useful fraction of the dense kernel's work
   int tile[3] = {4, 4, 8};       // dense MAC tile in parents
   bool order_by_list = false;    // dense MAC groups: parents ordered by neighbour set (FLGF_CTX_ORDER)
+  int mac = 1;                   // FP32 MAC form (FLGF_CTX_MAC): 1 frequency-lane, 0 parent groups + pair lists
   // failure injection (FLGF_CTX_FAIL_ALLOC): the fail_alloc_at-th block-set
   // device allocation from the arming on reports out-of-memory instead of allocating
   int fail_alloc_at = 0, alloc_count = 0;
@@ -155,6 +156,8 @@ struct PhaseOff {  // arena offsets and counts of one phase's launch lists
   int n_groups_dense = 0, n_work = 0, max_units = 0;
   size_t hgroups = 0, work = 0, src_ids = 0, tgt_ids = 0, par_tab = 0;
   int n_groups = 0, max_group_src = 0; size_t groups = 0, l_tgt = 0, l_len = 0, l_ent = 0, l_src = 0;
+  int n_fl = 0, fl_max_cells = 0, fl_max_parents = 0; size_t fl_groups = 0, fl_rows = 0, fl_tgt = 0, fl_cells = 0;
+  int fl_ncomp = 1, fl_cstride = 0;  // components sharing the frequency-lane groups, their column stride
   int n_inv = 0, n_inv0 = 0; size_t inv_sid = 0, inv_gid = 0, inv_scale = 0;  // finest octree level first (n_inv0)
   std::vector<int> n_itp; std::vector<size_t> itp_ch, itp_par, itp_cpos;
   int n_sel = 0; size_t sel_src = 0, sel_dst = 0;
@@ -217,6 +220,7 @@ struct flgf_blockset {
   bool use_graph = false, timing = false;
   bool compensated = false;  // FLGF_OPT_COMPENSATED (FP32 block sets)
   bool masked = false;       // created with a target mask (flgf_blockset_create_masked)
+  int ncomp = 1;             // components of a vector block set (flgf_blockset_create_vector)
   cudaGraphExec_t gexec = nullptr;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;  // (stage, (start, end))
   size_t ev_used = 0;
@@ -434,7 +438,8 @@ extern "C" void flgf_blockset_destroy(flgf_blockset* bs) {
 
 // FMM launch lists of phase l for the given instances (their is_src /
 // need_tgt masks select sources and targets), appended to arena ar.
-static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<const Inst*>& insts, PhaseOff& ph, bool count) {
+static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<const Inst*>& insts, PhaseOff& ph, bool count,
+                      int ncomp) {
   flgf_ctx* ctx = bs->ctx;
   const int N = ctx->N;
   const int TP[3] = {ctx->tile[0], ctx->tile[1], ctx->tile[2]};  // tile in parents (<= 128: 256 threads)
@@ -455,6 +460,14 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
   // targets of sparse tiles per octree level, in tile order: (target id, pair list)
   std::vector<std::vector<std::pair<int, std::vector<int>>>> lpool;
   const int nchunk = ctx->prec == FLGF_FP64 ? nchunks<double>(N) : nchunks<float>(N);
+  // FP32 frequency-lane MAC: the dense tiles' parents go to its groups (sparse
+  // tiles still to the pair lists)
+  const bool fl = ctx->prec == FLGF_FP32 && ctx->mac == 1;
+  // vector block set (identical meshes, problem c = component c): component
+  // 0's dense tiles serve every component through the component-sharing
+  // kernel, whose columns for component c are component 0's + c * cstride
+  const int vcomp = fl && ncomp == kFlvComponents ? ncomp : 1;
+  const int list_pct = ctx->list_pct;
   // interaction tiles of one (instance, octree level): the expensive part of
   // list building, run on the host's cores (see below)
   struct TileJob {
@@ -595,7 +608,7 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
                 }
                 recs.push_back(r);
               }
-          if (useful * 100 < (int64_t)ctx->list_pct * dense) {
+          if (useful * 100 < (int64_t)list_pct * dense) {
             // sparse tile: its targets join the pair-list pool of octree level k
             for (int ti = 0; ti < (int)tg.size(); ++ti)
               if (tg[ti] >= 0) job.lrecs.push_back({tg[ti], std::move(plist[ti])});
@@ -672,6 +685,7 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
   }
   for (TileJob& job : jobs) {
     if (count) bs->pairs += job.pairs;
+    if (vcomp > 1 && job.inp->p > 0) job.drecs.clear();  // component 0's groups serve it
     if (!job.drecs.empty()) {
       if ((int)dpool.size() <= job.k) dpool.resize(job.k + 1);
       dpool[job.k].insert(dpool[job.k].end(), job.drecs.begin(), job.drecs.end());
@@ -681,10 +695,24 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
       for (auto& r : job.lrecs) lpool[job.k].push_back(std::move(r));
     }
   }
-  // dense MAC: parent groups of every octree level
+  // dense MAC: parent groups of every octree level (or frequency-lane groups)
   HadLists hl;
-  for (int k = 0; k < (int)dpool.size(); ++k)
-    pack_parent_groups(k, dpool[k], nchunk, had_kernel_units(ctx->prec == FLGF_FP64), hl, ctx->order_by_list);
+  FlLists fll;
+  for (int k = 0; k < (int)dpool.size(); ++k) {
+    if (fl)
+      pack_fl_groups(k, dpool[k], fll);
+    else
+      pack_parent_groups(k, dpool[k], nchunk, had_kernel_units(ctx->prec == FLGF_FP64), hl, ctx->order_by_list);
+  }
+  ph.n_fl = (int)fll.groups.size();
+  ph.fl_ncomp = vcomp;
+  ph.fl_cstride = ph.nblocks / vcomp;
+  ph.fl_max_cells = fll.max_cells;
+  ph.fl_max_parents = fll.max_parents;
+  ph.fl_groups = ar.add(fll.groups);
+  ph.fl_rows = ar.add(fll.rows);
+  ph.fl_tgt = ar.add(fll.tgt_ids);
+  ph.fl_cells = ar.add(fll.cells);
   // pair-list groups: consecutive pool targets (spatially close, so their
   // source sets overlap) up to kListTargets targets or kListMaxSrc sources
   for (int k = 0; k < (int)lpool.size(); ++k) {
@@ -940,7 +968,7 @@ static int plan_blockset(flgf_ctx* ctx, flgf_blockset* bs, int n_problems, const
     std::vector<const Inst*> insts;
     for (const auto& in : bs->inst)
       if (in.l == l) insts.push_back(&in);
-    build_fmm(bs, ar, l, insts, ph, true);
+    build_fmm(bs, ar, l, insts, ph, true, bs->ncomp);
     // multi-resolution coupling lists
     std::vector<int> sel_src, sel_dst, selw_src, selw_dst, acc_nbr, acc_fine, acc_cpos, accw_nbr, accw_fine,
         accw_cpos, cor_nbr, cor_fine, cor_cpos, crs_c, crs_f;
@@ -1044,13 +1072,15 @@ static int plan_blockset(flgf_ctx* ctx, flgf_blockset* bs, int n_problems, const
 }
 
 static int blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
-                           const int32_t* coords, const double* h0, const uint8_t* want, flgf_blockset** out) {
+                           const int32_t* coords, const double* h0, const uint8_t* want, int ncomp,
+                           flgf_blockset** out) {
   if (!ctx || !out || n_problems < 1 || !n_levels || !nblk || !coords || !h0)
     return fail(ctx, FLGF_EINVAL, "blockset_create: bad arguments");
   *out = nullptr;
   auto bs = new (std::nothrow) flgf_blockset();
   if (!bs) return fail(ctx, FLGF_ENOMEM, "host allocation");
   bs->ctx = ctx;
+  bs->ncomp = ncomp;
   auto bail = [&](int code, const std::string& m) {
     flgf_blockset_destroy(bs);
     return fail(ctx, code, m);
@@ -1101,13 +1131,40 @@ static int blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, c
 
 extern "C" int flgf_blockset_create(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
                                     const int32_t* coords, const double* h0, flgf_blockset** out) {
-  return blockset_create(ctx, n_problems, n_levels, nblk, coords, h0, nullptr, out);
+  return blockset_create(ctx, n_problems, n_levels, nblk, coords, h0, nullptr, 1, out);
 }
 
 extern "C" int flgf_blockset_create_masked(flgf_ctx* ctx, int n_problems, const int* n_levels, const int* nblk,
                                            const int32_t* coords, const double* h0, const uint8_t* want,
                                            flgf_blockset** out) {
-  return blockset_create(ctx, n_problems, n_levels, nblk, coords, h0, want, out);
+  return blockset_create(ctx, n_problems, n_levels, nblk, coords, h0, want, 1, out);
+}
+
+extern "C" int flgf_blockset_create_vector(flgf_ctx* ctx, int n_components, int n_levels, const int* nblk,
+                                           const int32_t* coords, double h0, flgf_blockset** out) {
+  if (!ctx || !out || n_components < 1 || n_components > 64 || n_levels < 1 || !nblk || !coords)
+    return fail(ctx, FLGF_EINVAL, "blockset_create_vector: bad arguments");
+  int64_t nb = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    if (nblk[l] < 0) return fail(ctx, FLGF_EINVAL, "blockset_create_vector: negative block count");
+    nb += nblk[l];
+  }
+  // the components as problems on copies of one mesh
+  std::vector<int> nlev(n_components, n_levels), nb_all;
+  std::vector<int32_t> c_all;
+  std::vector<double> h_all(n_components, h0);
+  try {
+    nb_all.reserve((size_t)n_components * n_levels);
+    c_all.reserve((size_t)n_components * 3 * nb);
+    for (int c = 0; c < n_components; ++c) {
+      nb_all.insert(nb_all.end(), nblk, nblk + n_levels);
+      c_all.insert(c_all.end(), coords, coords + 3 * nb);
+    }
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, FLGF_ENOMEM, "host allocation");
+  }
+  return blockset_create(ctx, n_components, nlev.data(), nb_all.data(), c_all.data(), h_all.data(), nullptr,
+                         n_components, out);
 }
 
 // Adjoint plan, built on first use: the transposed leaf-only instances, their
@@ -1157,7 +1214,7 @@ static int build_adjoint(flgf_blockset* bs) {
       if (in.l == l) insts.push_back(&in);
     bs->aph[l].gid_begin = bs->ph[l].gid_begin;
     bs->aph[l].nblocks = bs->ph[l].nblocks;
-    build_fmm(bs, aar, l, insts, bs->aph[l], false);
+    build_fmm(bs, aar, l, insts, bs->aph[l], false, 1);
     AdjOff& ao = bs->adj[l];
     std::vector<int> pd, p1, p2, gd, g1, g2, td, t1, t2, c0n, c0f, c0c, c1n, c1f, c1c;
     std::vector<double> c1h;
@@ -1365,6 +1422,15 @@ cudaError_t enqueue_fmm(flgf_blockset* bs, const Arena& ar, const PhaseOff& ph, 
                                        ph.max_units, ar.at<int>(ph.src_ids), ar.at<int>(ph.tgt_ids),
                                        ar.at<uint16_t>(ph.par_tab), bs->spec, bs->acc, ph.nblocks, c->d_kspec,
                                        c->kstride, s));
+    if (ph.fl_ncomp > 1)
+      KRUN(ph.n_fl, launch_hadamard_flv(N, ph.fl_ncomp, ph.fl_cstride, ar.at<FlGroup>(ph.fl_groups), ph.n_fl,
+                                        ph.fl_max_cells, ph.fl_max_parents, ar.at<uint16_t>(ph.fl_rows),
+                                        ar.at<int>(ph.fl_tgt), ar.at<int>(ph.fl_cells), bs->spec, bs->acc,
+                                        ph.nblocks, c->d_kspec, c->kstride, s));
+    else
+      KRUN(ph.n_fl, launch_hadamard_fl(N, ar.at<FlGroup>(ph.fl_groups), ph.n_fl, ph.fl_max_cells, ph.fl_max_parents,
+                                       ar.at<uint16_t>(ph.fl_rows), ar.at<int>(ph.fl_tgt), ar.at<int>(ph.fl_cells),
+                                       bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
     KRUN(ph.n_groups, launch_hadamard_list<R>(N, ar.at<ListGroup>(ph.groups), ph.n_groups, ph.max_group_src,
                                               ar.at<int>(ph.l_tgt), ar.at<int>(ph.l_len), ar.at<int>(ph.l_ent),
                                               ar.at<int>(ph.l_src), bs->spec, bs->acc, ph.nblocks, c->d_kspec,
@@ -1534,6 +1600,10 @@ extern "C" int flgf_ctx_set_option(flgf_ctx* ctx, int key, int value) {
     case FLGF_CTX_LIST_PCT:
       if (value < 0 || value > 100) return fail(ctx, FLGF_EINVAL, "list percentage must be 0..100");
       ctx->list_pct = value;
+      return FLGF_OK;
+    case FLGF_CTX_MAC:
+      if (value != 0 && value != 1) return fail(ctx, FLGF_EINVAL, "FLGF_CTX_MAC takes 0 or 1");
+      ctx->mac = value;
       return FLGF_OK;
     case FLGF_CTX_ORDER:
       if (value != 0 && value != 1) return fail(ctx, FLGF_EINVAL, "FLGF_CTX_ORDER takes 0 or 1");

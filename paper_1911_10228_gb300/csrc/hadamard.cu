@@ -262,19 +262,34 @@ __global__ void __launch_bounds__(kListTargets * 2) hadamard_list_kernel(const L
   R ar[TT], ai[TT];
 #pragma unroll
   for (int t = 0; t < TT; ++t) { ar[t] = R(0); ai[t] = R(0); }
-#pragma unroll 4
-  for (int j = 0; j < n; ++j) {
-    const int w = __ldg(e + j * kListTargets);
-    const int4 fv = Fs[g * gr.nsrc + (w >> 9)];
-    const int4 kv = Ks[g * kNOff + (w & 511)];
-    const cplx<R>* f = reinterpret_cast<const cplx<R>*>(&fv);
-    const cplx<R>* k = reinterpret_cast<const cplx<R>*>(&kv);
+  // the pair entries stream from global memory in batches of kPre, the next
+  // batch in flight while the current one is multiplied (entries past the
+  // list's end are zero: source slot 0, offset 0, not used)
+  constexpr int kPre = 8;
+  int wcur[kPre], wnxt[kPre];
 #pragma unroll
-    for (int t = 0; t < TT; ++t) {
-      ar[t] = fma(k[t].re, f[t].re, ar[t]);
-      ar[t] = fma(-k[t].im, f[t].im, ar[t]);
-      ai[t] = fma(k[t].re, f[t].im, ai[t]);
-      ai[t] = fma(k[t].im, f[t].re, ai[t]);
+  for (int q = 0; q < kPre; ++q) wnxt[q] = q < n ? __ldg(e + q * kListTargets) : 0;
+  for (int j0 = 0; j0 < n; j0 += kPre) {
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      wcur[q] = wnxt[q];
+      wnxt[q] = j0 + kPre + q < n ? __ldg(e + (j0 + kPre + q) * kListTargets) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      if (j0 + q >= n) break;
+      const int w = wcur[q];
+      const int4 fv = Fs[g * gr.nsrc + (w >> 9)];
+      const int4 kv = Ks[g * kNOff + (w & 511)];
+      const cplx<R>* f = reinterpret_cast<const cplx<R>*>(&fv);
+      const cplx<R>* k = reinterpret_cast<const cplx<R>*>(&kv);
+#pragma unroll
+      for (int t = 0; t < TT; ++t) {
+        ar[t] = fma(k[t].re, f[t].re, ar[t]);
+        ar[t] = fma(-k[t].im, f[t].im, ar[t]);
+        ai[t] = fma(k[t].re, f[t].im, ai[t]);
+        ai[t] = fma(k[t].im, f[t].re, ai[t]);
+      }
     }
   }
   cplx<R>* o = acc + chunk_offset<R>(chunk, tgt[gr.tgt_off + ti], spec_blocks) + g * TT;

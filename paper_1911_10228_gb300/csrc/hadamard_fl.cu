@@ -1,0 +1,460 @@
+// a3, FP32: the spectrum multiply-accumulate with one frequency per lane
+// (Sec. 2.1, level interaction: each target block's spectrum collects
+// K^_{t-s} (.) F^_s over its near and influence lists).
+//
+// Mapping.  A CTA takes a group of at most kFlMaxParents target parents (the
+// parents whose children are targets) and a block of kFlFreq = 64
+// consecutive frequencies; a warp owns one parent at a time and lane l holds
+// frequencies 2l and 2l + 1 (16 bytes).  All lanes of a warp share the parent's list of
+// neighbour cells with sources and the child masks (which of the parent's 8
+// children are targets, which of a cell's 8 children are sources), so absent
+// cells and children are skipped by warp-uniform control flow: no lane idles
+// while another works.
+//
+// Memory.  Shared memory holds the 343 kernel spectra of the frequency block,
+// [343][64] (176 KB): a kernel read is a row of 64 consecutive frequencies
+// (conflict-free), and the group's tables (the spectrum columns of its cells'
+// children, the parents' neighbour lists and targets).  The source spectra
+// are read from global memory (L2, and L1 for cells shared by the CTA's
+// parents): a cell child's 64 frequencies are four 128-byte lines of the
+// chunked spectrum layout, one 16-byte load per lane, and the next cell's
+// sources are in flight while the current one is multiplied.  One CTA of
+// kFlWarps = 12 warps per SM.
+//
+// Per (parent, cell) the structure of the block-pair offsets is used as in
+// the parent-group kernel: the 8 x 8 (target a, source b) pairs of the parent
+// and the neighbour parent p + e take kernel offset d = (a - b) - 2e, so one
+// kernel-spectrum read serves every pair with the same a - b.  All 64 pairs
+// are unrolled when both child masks are full; otherwise each pair runs under
+// a warp-uniform test and kernel reads with no present pair are skipped.
+#include <algorithm>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace flgf {
+
+namespace {
+
+constexpr int kFlThreads = 32 * kFlWarps;
+
+// two frequencies: k, f hold (re, im) of frequency 0 in x, y and of frequency 1 in z, w
+__device__ __forceinline__ void cmac(float (&ar)[2], float (&ai)[2], float4 k, float4 f) {
+  ar[0] = fmaf(k.x, f.x, ar[0]);
+  ar[0] = fmaf(-k.y, f.y, ar[0]);
+  ai[0] = fmaf(k.x, f.y, ai[0]);
+  ai[0] = fmaf(k.y, f.x, ai[0]);
+  ar[1] = fmaf(k.z, f.z, ar[1]);
+  ar[1] = fmaf(-k.w, f.w, ar[1]);
+  ai[1] = fmaf(k.z, f.w, ai[1]);
+  ai[1] = fmaf(k.w, f.z, ai[1]);
+}
+
+// The 8 children of a cell (their spectrum columns in shared memory) at this
+// lane's frequency, zero where absent; returns the cell's source mask.  The
+// lane's offset into the chunked spectrum layout is fixed (lane_spec), a
+// source column adds 4 T complex values per column.
+// The loads are volatile inline PTX so that the compiler issues them where
+// they stand (one cell ahead of their use) instead of sinking them towards
+// the products; a load is predicated off for an absent child (sid < 0), which
+// keeps its zero.
+__device__ __forceinline__ float4 ld_cg_f4_if(const float4* p, int sid) {
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ge.s32 q, %5, 0;\n\t@q ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];\n\t}"
+      : "+f"(v.x), "+f"(v.y), "+f"(v.z), "+f"(v.w)
+      : "l"(p), "r"(sid));
+  return v;
+}
+__device__ __forceinline__ int load_cell(const int* cid, const float2* __restrict__ lane_spec, float4 (&f)[8]) {
+  int smask = 0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int sid = cid[b];
+    smask |= (sid >= 0) << b;
+    f[b] = ld_cg_f4_if(reinterpret_cast<const float4*>(lane_spec + (size_t)max(sid, 0) * (kChunkGroup * ChunkT<float>::value)),
+                       sid);
+  }
+  return smask;
+}
+
+// The products of one (parent, cell): kernel offset d = (a - b) - 2e.
+__device__ __forceinline__ void cell_products(const float4* __restrict__ Kc, int tmask, int smask, const float4 (&f)[8],
+                                              float (&ar)[8][2], float (&ai)[8][2]) {
+  if ((tmask & smask) == 0xFF) {
+    // both masks full: all 64 pairs, one kernel read per a - b
+#pragma unroll
+    for (int dl = 0; dl < 27; ++dl) {
+      const int l0 = dl / 9 - 1, l1 = (dl / 3) % 3 - 1, l2 = dl % 3 - 1;
+      const float4 k = Kc[(l0 * 49 + l1 * 7 + l2) * (kFlFreq / 2)];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int b0 = (a >> 2) - l0, b1 = ((a >> 1) & 1) - l1, b2 = (a & 1) - l2;
+        if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b2 < 0 || b2 > 1) continue;  // compile time
+        cmac(ar[a], ai[a], k, f[(b0 << 2) | (b1 << 1) | b2]);
+      }
+    }
+  } else {
+    // some children absent: each pair under a warp-uniform test
+    uint64_t pmask = 0;  // bit 8a + b: target a and source b both present
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if ((tmask >> a) & 1) pmask |= (uint64_t)smask << (8 * a);
+#pragma unroll
+    for (int dl = 0; dl < 27; ++dl) {
+      const int l0 = dl / 9 - 1, l1 = (dl / 3) % 3 - 1, l2 = dl % 3 - 1;
+      uint64_t dmask = 0;  // the pairs with a - b = delta (compile time)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int b0 = (a >> 2) - l0, b1 = ((a >> 1) & 1) - l1, b2 = (a & 1) - l2;
+        if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b2 < 0 || b2 > 1) continue;
+        dmask |= 1ull << (8 * a + ((b0 << 2) | (b1 << 1) | b2));
+      }
+      if (!(pmask & dmask)) continue;
+      const float4 k = Kc[(l0 * 49 + l1 * 7 + l2) * (kFlFreq / 2)];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int b0 = (a >> 2) - l0, b1 = ((a >> 1) & 1) - l1, b2 = (a & 1) - l2;
+        if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b2 < 0 || b2 > 1) continue;
+        const int b = (b0 << 2) | (b1 << 1) | b2;
+        if ((pmask >> (8 * a + b)) & 1) cmac(ar[a], ai[a], k, f[b]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ const float4* kernel_row(const float4* Ks, int w, int lane) {
+  const int e = w >> 11;
+  const int e0 = e / 9 - 1, e1 = (e / 3) % 3 - 1, e2 = e % 3 - 1;
+  return Ks + off_index(-2 * e0, -2 * e1, -2 * e2) * (kFlFreq / 2) + lane;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kFlThreads, 1)
+    hadamard_fl_kernel(const FlGroup* __restrict__ groups, int ngroups, const uint16_t* __restrict__ rows,
+                       const int* __restrict__ tgt_ids, const int* __restrict__ cells,
+                       const float2* __restrict__ spec, float2* __restrict__ acc, int spec_blocks,
+                       const float2* __restrict__ kspec, size_t kstride) {
+  constexpr int T = ChunkT<float>::value;  // 4 frequencies per chunk
+  constexpr int CPB = kFlFreq / T;         // 16 chunks per frequency block
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Ks = reinterpret_cast<float2*>(smem_raw);  // [343][64]
+  const int id = blockIdx.x;
+  const int g = id % ngroups, fb = id / ngroups;     // consecutive CTAs share the frequency block
+  const FlGroup gp = groups[g];
+  int* CI = reinterpret_cast<int*>(Ks + kNOff * kFlFreq);             // [ncell][8] spectrum columns
+  int* TG = CI + gp.ncell * 8;                                         // [nact][8] targets
+  uint16_t* PR = reinterpret_cast<uint16_t*>(TG + gp.nact * 8);       // [nact][kFlRowStride]
+  const int tid = threadIdx.x;
+  const int chunk0 = fb * CPB;
+
+  // kernel spectra of the block: CPB chunks of [343][T], contiguous in the table
+  {
+    const int4* src = reinterpret_cast<const int4*>(kspec + (size_t)gp.level * kstride + (size_t)chunk0 * kNOff * T);
+    constexpr int NV = CPB * kNOff * T / 2;  // 16-byte vectors (two complex values each)
+    for (int i = tid; i < NV; i += kFlThreads) {
+      const int4 v = __ldg(src + i);
+      const int idx = 2 * i;                 // [chunk][d][t], t even
+      const int c = idx / (kNOff * T), r = idx % (kNOff * T), d = r / T, t = r % T;
+      float2* dst = Ks + d * kFlFreq + c * T + t;
+      dst[0] = make_float2(__int_as_float(v.x), __int_as_float(v.y));
+      dst[1] = make_float2(__int_as_float(v.z), __int_as_float(v.w));
+    }
+  }
+  for (int i = tid; i < gp.ncell * 8; i += kFlThreads) CI[i] = __ldg(cells + (size_t)gp.cell_off * 8 + i);
+  for (int i = tid; i < gp.nact * 8; i += kFlThreads) TG[i] = __ldg(tgt_ids + (size_t)gp.row_off * 8 + i);
+  for (int i = tid; i < gp.nact * kFlRowStride; i += kFlThreads) PR[i] = __ldg(rows + (size_t)gp.row_off * kFlRowStride + i);
+  __syncthreads();
+
+  const int lane = tid & 31, warp = tid >> 5;
+  const int chunk = chunk0 + (2 * lane) / T, t = (2 * lane) % T;  // this lane's two frequencies (t even)
+  const float2* lane_spec = spec + chunk_offset<float>(chunk, 0, spec_blocks) + t;
+  float2* lane_acc = acc + chunk_offset<float>(chunk, 0, spec_blocks) + t;
+  const float4* Ks4 = reinterpret_cast<const float4*>(Ks);
+  for (int pm = warp; pm < gp.nact; pm += kFlWarps) {
+    const uint16_t* row = PR + pm * kFlRowStride;
+    const int* tg = TG + pm * 8;
+    const int ncl = row[0];
+    int tmask = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) tmask |= (tg[a] >= 0) << a;
+    float ar[8][2], ai[8][2];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) { ar[a][0] = ar[a][1] = 0.f; ai[a][0] = ai[a][1] = 0.f; }
+    // cells in pairs, ping-ponging two register buffers: the next cell's
+    // sources are in flight while the current one is multiplied
+    float4 fa[8], fb[8];
+    int sa = ncl > 0 ? load_cell(CI + 8 * (row[1] & 0x7FF), lane_spec, fa) : 0, sb = 0;
+    for (int j = 0; j < ncl; j += 2) {
+      if (j + 1 < ncl) sb = load_cell(CI + 8 * (row[2 + j] & 0x7FF), lane_spec, fb);
+      cell_products(kernel_row(Ks4, row[1 + j], lane), tmask, sa, fa, ar, ai);
+      if (j + 1 >= ncl) break;
+      if (j + 2 < ncl) sa = load_cell(CI + 8 * (row[3 + j] & 0x7FF), lane_spec, fa);
+      cell_products(kernel_row(Ks4, row[2 + j], lane), tmask, sb, fb, ar, ai);
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      if (!((tmask >> a) & 1)) continue;
+      *reinterpret_cast<float4*>(lane_acc + (size_t)tg[a] * (kChunkGroup * T)) =
+          make_float4(ar[a][0], ai[a][0], ar[a][1], ai[a][1]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Vector problems (several components on one mesh, e.g. the three Cartesian
+// components of a streamfunction, Sec. 3.1): a warp owns one parent for all
+// NC components, one frequency per lane (K^ rows of 32 frequencies, 88 KB),
+// so every kernel-spectrum read of a (parent, cell) serves the products of
+// every component.  Component c's spectrum columns are component 0's plus
+// c * cstride (the components' blocks are laid out alike).  Per component and
+// frequency the sums run in the same order as in the scalar kernel.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kFlvWarps = 8;
+constexpr int kFlvThreads = 32 * kFlvWarps;
+constexpr int kFlvFreq = 32;
+
+__device__ __forceinline__ void cmac1(float& ar, float& ai, float2 k, float2 f) {
+  ar = fmaf(k.x, f.x, ar);
+  ar = fmaf(-k.y, f.y, ar);
+  ai = fmaf(k.x, f.y, ai);
+  ai = fmaf(k.y, f.x, ai);
+}
+
+__device__ __forceinline__ float2 ld_cg_f2_if(const float2* p, int sid) {
+  float2 v = make_float2(0.f, 0.f);
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ge.s32 q, %3, 0;\n\t@q ld.global.cg.v2.f32 {%0, %1}, [%2];\n\t}"
+               : "+f"(v.x), "+f"(v.y)
+               : "l"(p), "r"(sid));
+  return v;
+}
+
+template <int NC>
+__device__ __forceinline__ int load_cell_v(const int* cid, const float2* __restrict__ lane_spec, int cstride,
+                                           float2 (&f)[NC][8]) {
+  int smask = 0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int sid = cid[b];
+    smask |= (sid >= 0) << b;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      f[c][b] = ld_cg_f2_if(lane_spec + (size_t)(max(sid, 0) + c * cstride) * (kChunkGroup * ChunkT<float>::value),
+                            sid);
+  }
+  return smask;
+}
+
+template <int NC>
+__device__ __forceinline__ void cell_products_v(const float2* __restrict__ Kc, int tmask, int smask,
+                                                const float2 (&f)[NC][8], float (&ar)[NC][8], float (&ai)[NC][8]) {
+  const bool full = (tmask & smask) == 0xFF;
+  uint64_t pmask = 0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+    if ((tmask >> a) & 1) pmask |= (uint64_t)smask << (8 * a);
+#pragma unroll
+  for (int dl = 0; dl < 27; ++dl) {
+    const int l0 = dl / 9 - 1, l1 = (dl / 3) % 3 - 1, l2 = dl % 3 - 1;
+    uint64_t dmask = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int b0 = (a >> 2) - l0, b1 = ((a >> 1) & 1) - l1, b2 = (a & 1) - l2;
+      if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b2 < 0 || b2 > 1) continue;
+      dmask |= 1ull << (8 * a + ((b0 << 2) | (b1 << 1) | b2));
+    }
+    if (!full && !(pmask & dmask)) continue;
+    const float2 k = Kc[(l0 * 49 + l1 * 7 + l2) * kFlvFreq];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int b0 = (a >> 2) - l0, b1 = ((a >> 1) & 1) - l1, b2 = (a & 1) - l2;
+      if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b2 < 0 || b2 > 1) continue;
+      const int b = (b0 << 2) | (b1 << 1) | b2;
+      if (full || ((pmask >> (8 * a + b)) & 1)) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) cmac1(ar[c][a], ai[c][a], k, f[c][b]);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+template <int NC>
+__global__ void __launch_bounds__(kFlvThreads, 1)
+    hadamard_flv_kernel(const FlGroup* __restrict__ groups, int ngroups, const uint16_t* __restrict__ rows,
+                        const int* __restrict__ tgt_ids, const int* __restrict__ cells, int cstride,
+                        const float2* __restrict__ spec, float2* __restrict__ acc, int spec_blocks,
+                        const float2* __restrict__ kspec, size_t kstride) {
+  constexpr int T = ChunkT<float>::value;
+  constexpr int CPB = kFlvFreq / T;  // 8 chunks per frequency block
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Ks = reinterpret_cast<float2*>(smem_raw);  // [343][32]
+  const int id = blockIdx.x;
+  const int g = id % ngroups, fb = id / ngroups;
+  const FlGroup gp = groups[g];
+  int* CI = reinterpret_cast<int*>(Ks + kNOff * kFlvFreq);
+  int* TG = CI + gp.ncell * 8;
+  uint16_t* PR = reinterpret_cast<uint16_t*>(TG + gp.nact * 8);
+  const int tid = threadIdx.x;
+  const int chunk0 = fb * CPB;
+  {
+    const int4* src = reinterpret_cast<const int4*>(kspec + (size_t)gp.level * kstride + (size_t)chunk0 * kNOff * T);
+    constexpr int NV = CPB * kNOff * T / 2;
+    for (int i = tid; i < NV; i += kFlvThreads) {
+      const int4 v = __ldg(src + i);
+      const int idx = 2 * i;
+      const int c = idx / (kNOff * T), r = idx % (kNOff * T), d = r / T, t = r % T;
+      float2* dst = Ks + d * kFlvFreq + c * T + t;
+      dst[0] = make_float2(__int_as_float(v.x), __int_as_float(v.y));
+      dst[1] = make_float2(__int_as_float(v.z), __int_as_float(v.w));
+    }
+  }
+  for (int i = tid; i < gp.ncell * 8; i += kFlvThreads) CI[i] = __ldg(cells + (size_t)gp.cell_off * 8 + i);
+  for (int i = tid; i < gp.nact * 8; i += kFlvThreads) TG[i] = __ldg(tgt_ids + (size_t)gp.row_off * 8 + i);
+  for (int i = tid; i < gp.nact * kFlRowStride; i += kFlvThreads)
+    PR[i] = __ldg(rows + (size_t)gp.row_off * kFlRowStride + i);
+  __syncthreads();
+
+  const int lane = tid & 31, warp = tid >> 5;
+  const int chunk = chunk0 + lane / T, t = lane % T;
+  const float2* lane_spec = spec + chunk_offset<float>(chunk, 0, spec_blocks) + t;
+  float2* lane_acc = acc + chunk_offset<float>(chunk, 0, spec_blocks) + t;
+  for (int pm = warp; pm < gp.nact; pm += kFlvWarps) {
+    const uint16_t* row = PR + pm * kFlRowStride;
+    const int* tg = TG + pm * 8;
+    const int ncl = row[0];
+    int tmask = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) tmask |= (tg[a] >= 0) << a;
+    float ar[NC][8], ai[NC][8];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) { ar[c][a] = 0.f; ai[c][a] = 0.f; }
+    float2 fa[NC][8], fb[NC][8];
+    int sa = ncl > 0 ? load_cell_v<NC>(CI + 8 * (row[1] & 0x7FF), lane_spec, cstride, fa) : 0, sb = 0;
+    for (int j = 0; j < ncl; j += 2) {
+      if (j + 1 < ncl) sb = load_cell_v<NC>(CI + 8 * (row[2 + j] & 0x7FF), lane_spec, cstride, fb);
+      {
+        const int e = row[1 + j] >> 11;
+        cell_products_v<NC>(Ks + off_index(-2 * (e / 9 - 1), -2 * ((e / 3) % 3 - 1), -2 * (e % 3 - 1)) * kFlvFreq + lane,
+                            tmask, sa, fa, ar, ai);
+      }
+      if (j + 1 >= ncl) break;
+      if (j + 2 < ncl) sa = load_cell_v<NC>(CI + 8 * (row[3 + j] & 0x7FF), lane_spec, cstride, fa);
+      {
+        const int e = row[2 + j] >> 11;
+        cell_products_v<NC>(Ks + off_index(-2 * (e / 9 - 1), -2 * ((e / 3) % 3 - 1), -2 * (e % 3 - 1)) * kFlvFreq + lane,
+                            tmask, sb, fb, ar, ai);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      if (!((tmask >> a) & 1)) continue;
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        lane_acc[(size_t)(tg[a] + c * cstride) * (kChunkGroup * T)] = make_float2(ar[c][a], ai[c][a]);
+    }
+  }
+}
+
+cudaError_t launch_hadamard_flv(int N, int ncomp, int cstride, const FlGroup* groups, int ngroups, int max_cells,
+                                int max_parents, const uint16_t* rows, const int* tgt_ids, const int* cells,
+                                const void* spec, void* acc, int spec_blocks, const void* kspec,
+                                size_t kspec_level_stride, cudaStream_t s) {
+  if (ngroups <= 0) return cudaSuccess;
+  if (ncomp != kFlvComponents) return cudaErrorInvalidValue;  // the one instantiation
+  const int nfb = nfreq(N) / kFlvFreq;
+  const size_t sm = sizeof(float2) * (size_t)kNOff * kFlvFreq + sizeof(int) * 8 * ((size_t)max_cells + max_parents) +
+                    sizeof(uint16_t) * (size_t)kFlRowStride * max_parents;
+  if (sm > kFlSmemBytes || (size_t)nfb * ngroups >= (1u << 31)) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(hadamard_flv_kernel<kFlvComponents>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  hadamard_flv_kernel<kFlvComponents><<<(unsigned)(nfb * ngroups), kFlvThreads, sm, s>>>(
+      groups, ngroups, rows, tgt_ids, cells, cstride, reinterpret_cast<const float2*>(spec),
+      reinterpret_cast<float2*>(acc), spec_blocks, reinterpret_cast<const float2*>(kspec), kspec_level_stride);
+  return cudaGetLastError();
+}
+
+size_t fl_smem_bytes(int max_cells, int max_parents) {
+  return sizeof(float2) * (size_t)kNOff * kFlFreq + sizeof(int) * 8 * ((size_t)max_cells + max_parents) +
+         sizeof(uint16_t) * (size_t)kFlRowStride * max_parents;
+}
+
+cudaError_t launch_hadamard_fl(int N, const FlGroup* groups, int ngroups, int max_cells, int max_parents,
+                               const uint16_t* rows, const int* tgt_ids, const int* cells, const void* spec, void* acc,
+                               int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s) {
+  if (ngroups <= 0) return cudaSuccess;
+  const int nfb = nfreq(N) / kFlFreq;
+  const size_t sm = fl_smem_bytes(max_cells, max_parents);
+  if (sm > kFlSmemBytes || (size_t)nfb * ngroups >= (1u << 31)) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(hadamard_fl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  hadamard_fl_kernel<<<(unsigned)(nfb * ngroups), kFlThreads, sm, s>>>(
+      groups, ngroups, rows, tgt_ids, cells, reinterpret_cast<const float2*>(spec), reinterpret_cast<float2*>(acc),
+      spec_blocks, reinterpret_cast<const float2*>(kspec), kspec_level_stride);
+  return cudaGetLastError();
+}
+
+static int fl_cell_key(const int* ch) {
+  for (int b = 0; b < 8; ++b)
+    if (ch[b] >= 0) return ch[b];
+  return -1;
+}
+
+void pack_fl_groups(int level, const std::vector<ParentRec>& recs, FlLists& L) {
+  size_t pos = 0;
+  while (pos < recs.size()) {
+    // consecutive parents (tile order, so they share cells) while the group's cells fit
+    std::unordered_map<int, int> cell_of;
+    std::vector<const int*> cells;
+    std::vector<size_t> members;
+    while (pos < recs.size() && (int)members.size() < kFlMaxParents) {
+      const ParentRec& r = recs[pos];
+      int add = 0;
+      for (int e = 0; e < 27; ++e) {
+        const int key = fl_cell_key(r.cell[e]);
+        add += key >= 0 && !cell_of.count(key);
+      }
+      if (!members.empty() && (int)cells.size() + add > kFlMaxCells) break;
+      for (int e = 0; e < 27; ++e) {
+        const int key = fl_cell_key(r.cell[e]);
+        if (key >= 0 && !cell_of.count(key)) {
+          cell_of.emplace(key, (int)cells.size());
+          cells.push_back(r.cell[e]);
+        }
+      }
+      members.push_back(pos++);
+    }
+    FlGroup gp;
+    gp.level = level;
+    gp.nact = (int)members.size();
+    gp.ncell = (int)cells.size();
+    gp.row_off = (int)(L.tgt_ids.size() / 8);
+    gp.cell_off = (int)(L.cells.size() / 8);
+    for (const int* ch : cells) L.cells.insert(L.cells.end(), ch, ch + 8);
+    for (size_t m : members) {
+      const ParentRec& r = recs[m];
+      L.tgt_ids.insert(L.tgt_ids.end(), r.tgt, r.tgt + 8);
+      std::vector<uint16_t> row(kFlRowStride, 0);
+      int n = 0;
+      for (int e = 0; e < 27; ++e) {
+        const int key = fl_cell_key(r.cell[e]);
+        if (key >= 0) row[1 + n++] = (uint16_t)((e << 11) | cell_of.at(key));
+      }
+      row[0] = (uint16_t)n;
+      L.rows.insert(L.rows.end(), row.begin(), row.end());
+    }
+    L.max_cells = std::max(L.max_cells, gp.ncell);
+    L.max_parents = std::max(L.max_parents, gp.nact);
+    L.groups.push_back(gp);
+  }
+}
+
+}  // namespace flgf

@@ -129,6 +129,47 @@ cudaError_t launch_hadamard_list(int N, const ListGroup* groups, int ngroups, in
                                  const int* len, const int* ent, const int* src, const void* spec, void* acc,
                                  int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s);
 
+// FP32 frequency-lane MAC (hadamard_fl.cu): a CTA takes a group of at most
+// kFlMaxParents consecutive target parents (with at most kFlMaxCells
+// neighbour cells) and a block of kFlFreq consecutive frequencies; a warp
+// owns one parent, a lane two consecutive frequencies.  Per parent a row of kFlRowStride
+// uint16: [0] = number of cells n, [1 .. n] = e << 11 | cell for its
+// neighbours e with sources, in increasing e; cell indexes the group's cell
+// table of the 8 children's spectrum columns (-1 where a child is no source).
+constexpr int kFlWarps = 12;
+constexpr int kFlMaxParents = 32;
+constexpr int kFlMaxCells = 768;
+constexpr int kFlFreq = 64;
+constexpr int kFlRowStride = 28;
+constexpr size_t kFlSmemBytes = 227 * 1024;  // one CTA per SM
+struct FlGroup {
+  int level;     // octree level (kernel spectra)
+  int nact;      // target parents
+  int ncell;     // neighbour cells with sources
+  int row_off;   // first parent: rows [row_off + m][kFlRowStride], targets [row_off + m][8]
+  int cell_off;  // first cell: [cell_off + c][8]
+};
+struct FlLists {
+  std::vector<FlGroup> groups;
+  std::vector<uint16_t> rows;  // [parents][kFlRowStride]
+  std::vector<int> tgt_ids;    // [parents][8] spectrum column or -1
+  std::vector<int> cells;      // [cells][8] spectrum column or -1
+  int max_cells = 0, max_parents = 0;
+};
+// Packs parent records, in order, into frequency-lane groups of one octree level.
+void pack_fl_groups(int level, const std::vector<ParentRec>& recs, FlLists& L);
+size_t fl_smem_bytes(int max_cells, int max_parents);
+cudaError_t launch_hadamard_fl(int N, const FlGroup* groups, int ngroups, int max_cells, int max_parents,
+                               const uint16_t* rows, const int* tgt_ids, const int* cells, const void* spec, void* acc,
+                               int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s);
+// The component-sharing form for vector block sets of kFlvComponents
+// components: the same groups, component c's spectrum columns at + c * cstride.
+constexpr int kFlvComponents = 3;
+cudaError_t launch_hadamard_flv(int N, int ncomp, int cstride, const FlGroup* groups, int ngroups, int max_cells,
+                                int max_parents, const uint16_t* rows, const int* tgt_ids, const int* cells,
+                                const void* spec, void* acc, int spec_blocks, const void* kspec,
+                                size_t kspec_level_stride, cudaStream_t s);
+
 // ---- a1/a5 and multi-resolution stencils (stencil.cu) ----------------------
 // J1: dense 1-D Lagrange matrix [2N][N] (row = child node of the two children, column = parent node).
 template <typename R>

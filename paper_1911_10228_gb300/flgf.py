@@ -62,6 +62,8 @@ PROTOTYPES = {
     "flgf_blockset_create_masked": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_int_p, _c_int_p, _c_i32_p,
                                                    _c_dbl_p, ctypes.POINTER(ctypes.c_uint8),
                                                    ctypes.POINTER(ctypes.c_void_p)]),
+    "flgf_blockset_create_vector": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_int_p, _c_i32_p,
+                                                   ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
     "flgf_blockset_destroy": (None, [ctypes.c_void_p]),
     "flgf_blockset_dof": (ctypes.c_int64, [ctypes.c_void_p]),
     "flgf_load_source": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
@@ -215,7 +217,10 @@ class BlockSet:
     needed (a shard of a multi-GPU solve); the others are left unspecified.
     """
 
-    def __init__(self, ctx: Context, problems, h0, want=None):
+    def __init__(self, ctx: Context, problems, h0, want=None, vector: bool = False):
+        """vector: the problems are the components of one vector field on one
+        mesh (flgf_blockset_create_vector): every entry of problems must be the
+        same mesh and every h0 the same spacing."""
         self.ctx = ctx
         self.lib = ctx.lib
         self.levels = [[np.asarray(c, dtype=np.int32).reshape(-1, 3) for c in p] for p in problems]
@@ -227,7 +232,18 @@ class BlockSet:
             raise ValueError("one h0 per problem")
         h = ctypes.c_void_p()
         with torch.cuda.device(ctx.device):
-            if want is None:
+            if vector:
+                first = self.levels[0]
+                if want is not None or np.any(h0 != h0[0]) or any(
+                        len(p) != len(first) or any(not np.array_equal(a, b) for a, b in zip(p, first))
+                        for p in self.levels):
+                    raise ValueError("a vector block set takes one mesh, one h0 and no target mask")
+                c0 = np.ascontiguousarray(np.concatenate(first, axis=0).astype(np.int32))
+                nb0 = np.array([c.shape[0] for c in first], dtype=np.int32)
+                rc = self.lib.flgf_blockset_create_vector(ctx.handle, len(self.levels), len(first),
+                                                          _ptr(nb0, ctypes.c_int), _ptr(c0, ctypes.c_int32),
+                                                          float(h0[0]), ctypes.byref(h))
+            elif want is None:
                 rc = self.lib.flgf_blockset_create(ctx.handle, len(self.levels), _ptr(nlev, ctypes.c_int),
                                                    _ptr(nblk, ctypes.c_int), _ptr(coords, ctypes.c_int32),
                                                    _ptr(h0, ctypes.c_double), ctypes.byref(h))
@@ -390,11 +406,12 @@ def solve_problem(ctx: Context, prob, correction: bool = True, compensated: bool
 def solve_vector(ctx: Context, coords_levels, h0: float, components, correction: bool = True) -> list:
     """Vector Poisson problem (each Cartesian component of a field, e.g. the
     streamfunction of a vorticity field, is a scalar problem on the same mesh):
-    all components run as problems of one block set, so every stage of every
-    component shares the same kernel launches and the same cached kernel
-    spectra.  components[c][l] is component c's source on level l; returns the
+    all components run as problems of one vector block set, so every stage of
+    every component shares the same kernel launches and the same cached kernel
+    spectra, and the spectrum products of three FP32 components share their
+    kernel-spectrum reads.  components[c][l] is component c's source on level l; returns the
     potentials as components[c][l] device tensors."""
-    bs = BlockSet(ctx, [coords_levels] * len(components), [h0] * len(components))
+    bs = BlockSet(ctx, [coords_levels] * len(components), [h0] * len(components), vector=True)
     try:
         if not correction:
             bs.set_option(OPT_CORRECTION, 0)

@@ -8,7 +8,12 @@
 // level.  The forward phases and the adjoint phases (transposed leaf-only
 // instances) are checked.  The planning runs on the CPU.
 //
-// usage: planner_check <mesh file> <list_pct> <t0> <t1> <t2> <fp64 0|1>
+// usage: planner_check <mesh file> <list_pct> <t0> <t1> <t2> <fp64 0|1> [mac 0|1 [ncomp]]
+// (mac: the FP32 spectrum-MAC form, 1 = frequency-lane groups, 0 = parent
+// groups and pair lists; FP64 always uses the latter.  ncomp > 1: the
+// problems are the components of a vector block set, whose identical meshes
+// the file must hold; component 0's frequency-lane groups then stand for
+// every component, at columns + c * cstride)
 // mesh file (int32): N, n_problems, n_levels[n_problems], nblk[sum levels],
 // coords[3 * sum nblk]
 #include "../../paper_1911_10228_gb300/csrc/flgf_api.cu"
@@ -19,7 +24,7 @@
 #include <tuple>
 
 int main(int argc, char** argv) {
-  if (argc != 7) {
+  if (argc < 7 || argc > 9) {
     fprintf(stderr, "usage: %s mesh list_pct t0 t1 t2 fp64\n", argv[0]);
     return 2;
   }
@@ -47,9 +52,11 @@ int main(int argc, char** argv) {
   ctx.prec = atoi(argv[6]) ? FLGF_FP64 : FLGF_FP32;
   ctx.max_oct = 8;
   ctx.list_pct = atoi(argv[2]);
+  ctx.mac = argc >= 8 ? atoi(argv[7]) : 1;
   for (int a = 0; a < 3; ++a) ctx.tile[a] = atoi(argv[3 + a]);
   auto bs = new flgf_blockset();
   bs->ctx = &ctx;
+  bs->ncomp = argc == 9 ? atoi(argv[8]) : 1;
   const int rc = plan_blockset(&ctx, bs, np, nlev.data(), nblk.data(), coords.data(), h0.data());
   if (rc != FLGF_OK) {
     printf("plan failed (%d): %s\n", rc, ctx.err.c_str());
@@ -113,6 +120,53 @@ int main(int argc, char** argv) {
               if (g.level > 0 && std::abs(d0) <= 1 && std::abs(d1) <= 1 && std::abs(d2) <= 1) continue;
               got[Pair(t, s, off_index(d0, d1, d2))]++;
               ++dense_pairs;
+            }
+          }
+        }
+      }
+    }
+    // frequency-lane groups
+    const FlGroup* FG = reinterpret_cast<const FlGroup*>(base + ph.fl_groups);
+    const uint16_t* frows = reinterpret_cast<const uint16_t*>(base + ph.fl_rows);
+    const int* ftgt0 = reinterpret_cast<const int*>(base + ph.fl_tgt);
+    const int* fcells0 = reinterpret_cast<const int*>(base + ph.fl_cells);
+    for (int gi = 0; gi < ph.n_fl; ++gi) {
+      const FlGroup& g = FG[gi];
+      bad += g.nact < 1 || g.nact > kFlMaxParents || g.nact > ph.fl_max_parents || g.ncell > kFlMaxCells ||
+             g.ncell > ph.fl_max_cells;
+      const int* ftgt = ftgt0 + (size_t)g.row_off * 8;
+      const int* fcells = fcells0 + (size_t)g.cell_off * 8;
+      for (int m = 0; m < g.nact; ++m) {
+        for (int a = 0; a < 8; ++a) {
+          const int t = ftgt[m * 8 + a];
+          if (t < 0) continue;
+          for (int c = 0; c < ph.fl_ncomp; ++c) {
+            const int tc = t + c * ph.fl_cstride;
+            written[tc]++;
+            bad += tlevel.count(tc) == 0 || tlevel[tc] != g.level;
+          }
+        }
+        const uint16_t* row = frows + (size_t)(g.row_off + m) * kFlRowStride;
+        const int n = row[0];
+        if (n > 27) { ++bad; continue; }
+        int last_e = -1;
+        for (int j = 0; j < n; ++j) {
+          const int e = row[1 + j] >> 11, c = row[1 + j] & 0x7FF;
+          if (e <= last_e || e > 26 || c >= g.ncell) { ++bad; continue; }
+          last_e = e;
+          const int e0 = e / 9 - 1, e1 = (e / 3) % 3 - 1, e2 = e % 3 - 1;
+          for (int b = 0; b < 8; ++b) {
+            const int s = fcells[c * 8 + b];
+            if (s < 0) continue;
+            for (int a = 0; a < 8; ++a) {
+              const int t = ftgt[m * 8 + a];
+              if (t < 0) continue;
+              const int d0 = (a >> 2) - (b >> 2) - 2 * e0, d1 = ((a >> 1) & 1) - ((b >> 1) & 1) - 2 * e1,
+                        d2 = (a & 1) - (b & 1) - 2 * e2;
+              if (g.level > 0 && std::abs(d0) <= 1 && std::abs(d1) <= 1 && std::abs(d2) <= 1) continue;
+              for (int cc = 0; cc < ph.fl_ncomp; ++cc)
+                got[Pair(t + cc * ph.fl_cstride, s + cc * ph.fl_cstride, off_index(d0, d1, d2))]++;
+              dense_pairs += ph.fl_ncomp;
             }
           }
         }

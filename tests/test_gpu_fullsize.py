@@ -12,6 +12,8 @@
   the FP32 form agrees with the FP64 solve and with the FP64 oracle at
   sampled cells (tests/golden/torus128_oracle.txt) within 1e-5.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -131,3 +133,32 @@ def test_batched_full_size_sampled_problems_match_oracle():
                 assert err < tol, (precision, i, l, err)
         bs.close()
         ctx.close()
+
+
+def _golden_torus():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "torus128_oracle.txt")
+    umax, rows = None, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("umax"):
+                umax = float(line.split()[1])
+            elif line.strip() and not line.startswith("#"):
+                l, b, i, j, k, v = line.split()
+                rows.append((int(l), int(b), int(i), int(j), int(k), float(v)))
+    return umax, rows
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_torus_full_size_matches_oracle_samples(precision, tol):
+    """The 3-level torus in full (21 M DoF) against the FP64 oracle's values at
+    sampled cells of sampled leaf blocks of every level, corners included
+    (tests/golden/torus128_oracle.txt, written by make_torus128_oracle.py),
+    relative to the oracle's largest |u| on leaf cells."""
+    umax, rows = _golden_torus()
+    p = config_torus_128()
+    ctx = F.Context(N=16, n_interp=6, precision=precision)
+    u = [x.double().cpu().numpy() for x in F.solve_problem(ctx, p)]
+    err = max(abs(u[l][b, i, j, k] - v) for l, b, i, j, k, v in rows) / umax
+    print(f"torus {precision}: max |u - oracle| / max|u| over {len(rows)} sampled cells = {err:.3e}")
+    assert err < tol
+    ctx.close()
