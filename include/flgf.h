@@ -103,13 +103,17 @@ void flgf_destroy(flgf_ctx* ctx);
  *                      Tiles are the unit of the pair-list decision, and
  *                      their order is the order in which parents are packed
  *                      into the dense kernel's groups.
- *   FLGF_CTX_MAC       FP32 contexts: 1 (default) runs the spectrum MAC with one
- *                      frequency per thread and one target parent per warp
- *                      (absent cells and children are skipped warp-uniformly;
- *                      FLGF_CTX_LIST_PCT and FLGF_CTX_ORDER do not apply);
- *                      0 runs the parent-group kernel (one parent per thread)
- *                      and the pair-list kernel.  FP64 contexts always use the
- *                      latter.
+ *   FLGF_CTX_MAC       FP32 contexts: the kernels of the spectrum MAC.
+ *                      1 (default): dense tiles with one target parent per
+ *                      warp and one or two frequencies per thread (absent
+ *                      cells and children are skipped warp-uniformly), sparse
+ *                      tiles (FLGF_CTX_LIST_PCT) as pair lists with one target
+ *                      per warp and one frequency per thread; 2: the same
+ *                      dense kernel, sparse tiles in the shared-memory
+ *                      pair-list kernel (one target per thread); 0: the
+ *                      parent-group kernel (one parent per thread) and the
+ *                      shared-memory pair-list kernel.  FP64 contexts always
+ *                      use form 0; FLGF_CTX_ORDER applies to form 0 only.
  *   FLGF_CTX_ORDER     0 (default): the parents of each dense-kernel group keep
  *                      the tile order; 1: they are ordered by their set of
  *                      neighbours with sources (most first, equal sets

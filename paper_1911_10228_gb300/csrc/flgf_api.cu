@@ -24,7 +24,8 @@ struct flgf_ctx {
   int list_pct = 30;             // pair-list MAC below this useful fraction of the dense kernel's work
   int tile[3] = {4, 4, 8};       // dense MAC tile in parents
   bool order_by_list = false;    // dense MAC groups: parents ordered by neighbour set (FLGF_CTX_ORDER)
-  int mac = 1;                   // FP32 MAC form (FLGF_CTX_MAC): 1 frequency-lane, 0 parent groups + pair lists
+  int mac = 1;                   // FP32 MAC form (FLGF_CTX_MAC): 1 frequency-lane (dense and lists), 2 frequency-lane
+                                 // dense + shared-memory lists, 0 parent groups + shared-memory lists
   // failure injection (FLGF_CTX_FAIL_ALLOC): the fail_alloc_at-th block-set
   // device allocation from the arming on reports out-of-memory instead of allocating
   int fail_alloc_at = 0, alloc_count = 0;
@@ -156,8 +157,10 @@ struct PhaseOff {  // arena offsets and counts of one phase's launch lists
   int n_groups_dense = 0, n_work = 0, max_units = 0;
   size_t hgroups = 0, work = 0, src_ids = 0, tgt_ids = 0, par_tab = 0;
   int n_groups = 0, max_group_src = 0; size_t groups = 0, l_tgt = 0, l_len = 0, l_ent = 0, l_src = 0;
-  int n_fl = 0, fl_max_cells = 0, fl_max_parents = 0; size_t fl_groups = 0, fl_rows = 0, fl_tgt = 0, fl_cells = 0;
+  int n_fl = 0, fl_max_cells = 0, fl_max_parents = 0;
+  size_t fl_groups = 0, fl_rows = 0, fl_dlms = 0, fl_tgt = 0, fl_cells = 0;
   int fl_ncomp = 1, fl_cstride = 0;  // components sharing the frequency-lane groups, their column stride
+  int n_fll = 0; size_t fll_groups = 0, fll_tgt = 0, fll_beg = 0, fll_len = 0, fll_ent = 0;
   int n_inv = 0, n_inv0 = 0; size_t inv_sid = 0, inv_gid = 0, inv_scale = 0;  // finest octree level first (n_inv0)
   std::vector<int> n_itp; std::vector<size_t> itp_ch, itp_par, itp_cpos;
   int n_sel = 0; size_t sel_src = 0, sel_dst = 0;
@@ -462,7 +465,10 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
   const int nchunk = ctx->prec == FLGF_FP64 ? nchunks<double>(N) : nchunks<float>(N);
   // FP32 frequency-lane MAC: the dense tiles' parents go to its groups (sparse
   // tiles still to the pair lists)
-  const bool fl = ctx->prec == FLGF_FP32 && ctx->mac == 1;
+  const bool fl = ctx->prec == FLGF_FP32 && ctx->mac >= 1;
+  // FP32 pair lists of sparse tiles in frequency lanes (mac 1) or in the
+  // shared-memory pair-list kernel (mac 0 and 2)
+  const bool fll_lists = ctx->prec == FLGF_FP32 && ctx->mac == 1;
   // vector block set (identical meshes, problem c = component c): component
   // 0's dense tiles serve every component through the component-sharing
   // kernel, whose columns for component c are component 0's + c * cstride
@@ -711,8 +717,20 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
   ph.fl_max_parents = fll.max_parents;
   ph.fl_groups = ar.add(fll.groups);
   ph.fl_rows = ar.add(fll.rows);
+  ph.fl_dlms = ar.add(fll.dlms);
   ph.fl_tgt = ar.add(fll.tgt_ids);
   ph.fl_cells = ar.add(fll.cells);
+  FllLists fq;
+  if (fll_lists) {
+    for (int k = 0; k < (int)lpool.size(); ++k) pack_fll_groups(k, lpool[k], fq);
+    lpool.clear();
+  }
+  ph.n_fll = (int)fq.groups.size();
+  ph.fll_groups = ar.add(fq.groups);
+  ph.fll_tgt = ar.add(fq.tgt);
+  ph.fll_beg = ar.add(fq.beg);
+  ph.fll_len = ar.add(fq.len);
+  ph.fll_ent = ar.add(fq.ent);
   // pair-list groups: consecutive pool targets (spatially close, so their
   // source sets overlap) up to kListTargets targets or kListMaxSrc sources
   for (int k = 0; k < (int)lpool.size(); ++k) {
@@ -1425,11 +1443,15 @@ cudaError_t enqueue_fmm(flgf_blockset* bs, const Arena& ar, const PhaseOff& ph, 
     if (ph.fl_ncomp > 1)
       KRUN(ph.n_fl, launch_hadamard_flv(N, ph.fl_ncomp, ph.fl_cstride, ar.at<FlGroup>(ph.fl_groups), ph.n_fl,
                                         ph.fl_max_cells, ph.fl_max_parents, ar.at<uint16_t>(ph.fl_rows),
-                                        ar.at<int>(ph.fl_tgt), ar.at<int>(ph.fl_cells), bs->spec, bs->acc,
+                                        ar.at<uint32_t>(ph.fl_dlms), ar.at<int>(ph.fl_tgt), ar.at<int>(ph.fl_cells), bs->spec, bs->acc,
                                         ph.nblocks, c->d_kspec, c->kstride, s));
     else
       KRUN(ph.n_fl, launch_hadamard_fl(N, ar.at<FlGroup>(ph.fl_groups), ph.n_fl, ph.fl_max_cells, ph.fl_max_parents,
-                                       ar.at<uint16_t>(ph.fl_rows), ar.at<int>(ph.fl_tgt), ar.at<int>(ph.fl_cells),
+                                       ar.at<uint16_t>(ph.fl_rows), ar.at<uint32_t>(ph.fl_dlms), ar.at<int>(ph.fl_tgt),
+                                       ar.at<int>(ph.fl_cells),
+                                       bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
+    KRUN(ph.n_fll, launch_hadamard_fll(N, ar.at<FllGroup>(ph.fll_groups), ph.n_fll, ar.at<int>(ph.fll_tgt),
+                                       ar.at<int>(ph.fll_beg), ar.at<int>(ph.fll_len), ar.at<uint32_t>(ph.fll_ent),
                                        bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
     KRUN(ph.n_groups, launch_hadamard_list<R>(N, ar.at<ListGroup>(ph.groups), ph.n_groups, ph.max_group_src,
                                               ar.at<int>(ph.l_tgt), ar.at<int>(ph.l_len), ar.at<int>(ph.l_ent),
@@ -1602,7 +1624,7 @@ extern "C" int flgf_ctx_set_option(flgf_ctx* ctx, int key, int value) {
       ctx->list_pct = value;
       return FLGF_OK;
     case FLGF_CTX_MAC:
-      if (value != 0 && value != 1) return fail(ctx, FLGF_EINVAL, "FLGF_CTX_MAC takes 0 or 1");
+      if (value < 0 || value > 2) return fail(ctx, FLGF_EINVAL, "FLGF_CTX_MAC takes 0, 1 or 2");
       ctx->mac = value;
       return FLGF_OK;
     case FLGF_CTX_ORDER:

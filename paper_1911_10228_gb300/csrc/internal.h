@@ -134,13 +134,17 @@ cudaError_t launch_hadamard_list(int N, const ListGroup* groups, int ngroups, in
 // neighbour cells) and a block of kFlFreq consecutive frequencies; a warp
 // owns one parent, a lane two consecutive frequencies.  Per parent a row of kFlRowStride
 // uint16: [0] = number of cells n, [1 .. n] = e << 11 | cell for its
-// neighbours e with sources, in increasing e; cell indexes the group's cell
+// neighbours e with products, in increasing e; cell indexes the group's cell
 // table of the 8 children's spectrum columns (-1 where a child is no source).
-constexpr int kFlWarps = 12;
-constexpr int kFlMaxParents = 32;
+// Beside it kFlDelta uint32 delta masks, entry j for row entry 1 + j: bit
+// ((l0 + 1) * 3 + l1 + 1) * 3 + l2 + 1 set when a target-source child pair
+// with a - b = l contributes, bit 31 when all 27 may run (fl_delta_mask).
+constexpr int kFlWarps = 16;
+constexpr int kFlMaxParents = 64;
 constexpr int kFlMaxCells = 768;
 constexpr int kFlFreq = 64;
 constexpr int kFlRowStride = 28;
+constexpr int kFlDelta = kFlRowStride - 1;
 constexpr size_t kFlSmemBytes = 227 * 1024;  // one CTA per SM
 struct FlGroup {
   int level;     // octree level (kernel spectra)
@@ -152,22 +156,49 @@ struct FlGroup {
 struct FlLists {
   std::vector<FlGroup> groups;
   std::vector<uint16_t> rows;  // [parents][kFlRowStride]
+  std::vector<uint32_t> dlms;  // [parents][kFlDelta] delta masks of the row entries
   std::vector<int> tgt_ids;    // [parents][8] spectrum column or -1
   std::vector<int> cells;      // [cells][8] spectrum column or -1
   int max_cells = 0, max_parents = 0;
 };
 // Packs parent records, in order, into frequency-lane groups of one octree level.
 void pack_fl_groups(int level, const std::vector<ParentRec>& recs, FlLists& L);
+uint32_t fl_delta_mask(int level, int e, const int* tgt, const int* src);
 size_t fl_smem_bytes(int max_cells, int max_parents);
 cudaError_t launch_hadamard_fl(int N, const FlGroup* groups, int ngroups, int max_cells, int max_parents,
-                               const uint16_t* rows, const int* tgt_ids, const int* cells, const void* spec, void* acc,
-                               int spec_blocks, const void* kspec, size_t kspec_level_stride, cudaStream_t s);
+                               const uint16_t* rows, const uint32_t* dlms, const int* tgt_ids, const int* cells,
+                               const void* spec, void* acc, int spec_blocks, const void* kspec,
+                               size_t kspec_level_stride, cudaStream_t s);
+// FP32 frequency-lane pair lists (hadamard_fl.cu), for the targets of sparse
+// tiles: a CTA takes a group of at most kFllTargets targets and a block of
+// kFllFreq consecutive frequencies, a warp one target at a time, a lane one
+// frequency.  Target i of the phase has its spectrum column tgt[i] and the
+// entries ent[beg[i] .. beg[i] + len[i]) = source column << 9 | kernel offset
+// index (the pair-list pool's own format).
+constexpr int kFllWarps = 16;
+constexpr int kFllFreq = 32;
+constexpr int kFllTargets = 64;
+struct FllGroup {
+  int level;    // octree level (kernel spectra)
+  int ntgt;     // targets (<= kFllTargets), longest list first
+  int tgt_off;  // first target index
+};
+struct FllLists {
+  std::vector<FllGroup> groups;
+  std::vector<int> tgt, beg, len;
+  std::vector<uint32_t> ent;
+};
+// Packs the pair-list pool of one octree level, in order, into groups.
+void pack_fll_groups(int level, const std::vector<std::pair<int, std::vector<int>>>& pool, FllLists& L);
+cudaError_t launch_hadamard_fll(int N, const FllGroup* groups, int ngroups, const int* tgt, const int* beg,
+                                const int* len, const uint32_t* ent, const void* spec, void* acc, int spec_blocks,
+                                const void* kspec, size_t kspec_level_stride, cudaStream_t s);
 // The component-sharing form for vector block sets of kFlvComponents
 // components: the same groups, component c's spectrum columns at + c * cstride.
 constexpr int kFlvComponents = 3;
 cudaError_t launch_hadamard_flv(int N, int ncomp, int cstride, const FlGroup* groups, int ngroups, int max_cells,
-                                int max_parents, const uint16_t* rows, const int* tgt_ids, const int* cells,
-                                const void* spec, void* acc, int spec_blocks, const void* kspec,
+                                int max_parents, const uint16_t* rows, const uint32_t* dlms, const int* tgt_ids,
+                                const int* cells, const void* spec, void* acc, int spec_blocks, const void* kspec,
                                 size_t kspec_level_stride, cudaStream_t s);
 
 // ---- a1/a5 and multi-resolution stencils (stencil.cu) ----------------------

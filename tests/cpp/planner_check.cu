@@ -8,9 +8,10 @@
 // level.  The forward phases and the adjoint phases (transposed leaf-only
 // instances) are checked.  The planning runs on the CPU.
 //
-// usage: planner_check <mesh file> <list_pct> <t0> <t1> <t2> <fp64 0|1> [mac 0|1 [ncomp]]
-// (mac: the FP32 spectrum-MAC form, 1 = frequency-lane groups, 0 = parent
-// groups and pair lists; FP64 always uses the latter.  ncomp > 1: the
+// usage: planner_check <mesh file> <list_pct> <t0> <t1> <t2> <fp64 0|1> [mac 0|1|2 [ncomp]]
+// (mac: the FP32 spectrum-MAC form, FLGF_CTX_MAC: 1 = frequency-lane groups
+// and frequency-lane pair lists, 2 = frequency-lane groups and shared-memory
+// pair lists, 0 = parent groups and pair lists; FP64 always uses 0.  ncomp > 1: the
 // problems are the components of a vector block set, whose identical meshes
 // the file must hold; component 0's frequency-lane groups then stand for
 // every component, at columns + c * cstride)
@@ -128,6 +129,7 @@ int main(int argc, char** argv) {
     // frequency-lane groups
     const FlGroup* FG = reinterpret_cast<const FlGroup*>(base + ph.fl_groups);
     const uint16_t* frows = reinterpret_cast<const uint16_t*>(base + ph.fl_rows);
+    const uint32_t* fdlm = reinterpret_cast<const uint32_t*>(base + ph.fl_dlms);
     const int* ftgt0 = reinterpret_cast<const int*>(base + ph.fl_tgt);
     const int* fcells0 = reinterpret_cast<const int*>(base + ph.fl_cells);
     for (int gi = 0; gi < ph.n_fl; ++gi) {
@@ -155,6 +157,10 @@ int main(int argc, char** argv) {
           if (e <= last_e || e > 26 || c >= g.ncell) { ++bad; continue; }
           last_e = e;
           const int e0 = e / 9 - 1, e1 = (e / 3) % 3 - 1, e2 = e % 3 - 1;
+          // the delta mask: exactly the differences a - b of contributing pairs
+          const uint32_t dword = fdlm[(size_t)(g.row_off + m) * kFlDelta + j];
+          const uint32_t dmask = dword & ((1u << 27) - 1);
+          uint32_t seen = 0;
           for (int b = 0; b < 8; ++b) {
             const int s = fcells[c * 8 + b];
             if (s < 0) continue;
@@ -164,11 +170,45 @@ int main(int argc, char** argv) {
               const int d0 = (a >> 2) - (b >> 2) - 2 * e0, d1 = ((a >> 1) & 1) - ((b >> 1) & 1) - 2 * e1,
                         d2 = (a & 1) - (b & 1) - 2 * e2;
               if (g.level > 0 && std::abs(d0) <= 1 && std::abs(d1) <= 1 && std::abs(d2) <= 1) continue;
+              const int dl = (((a >> 2) - (b >> 2) + 1) * 3 + (((a >> 1) & 1) - ((b >> 1) & 1) + 1)) * 3 +
+                             ((a & 1) - (b & 1) + 1);
+              seen |= 1u << dl;
+              if (!((dmask >> dl) & 1u)) { ++bad; continue; }  // the kernel would skip this pair
               for (int cc = 0; cc < ph.fl_ncomp; ++cc)
                 got[Pair(t + cc * ph.fl_cstride, s + cc * ph.fl_cstride, off_index(d0, d1, d2))]++;
               dense_pairs += ph.fl_ncomp;
             }
           }
+          bad += seen != dmask;  // no delta without a product, and rows without products are dropped
+          bad += (dword >> 27) != 0 && (dword >> 27) != 16;  // bits 27-30 clear
+          if (dword >> 31) {  // a full row: every other delta is a near one of a coarse level
+            for (int dl = 0; dl < 27; ++dl) {
+              if ((dmask >> dl) & 1u) continue;
+              const int d0 = dl / 9 - 1 - 2 * e0, d1 = (dl / 3) % 3 - 1 - 2 * e1, d2 = dl % 3 - 1 - 2 * e2;
+              bad += !(g.level > 0 && std::abs(d0) <= 1 && std::abs(d1) <= 1 && std::abs(d2) <= 1);
+            }
+          }
+        }
+      }
+    }
+    // frequency-lane pair lists
+    const FllGroup* QG = reinterpret_cast<const FllGroup*>(base + ph.fll_groups);
+    const int* qt = reinterpret_cast<const int*>(base + ph.fll_tgt);
+    const int* qb = reinterpret_cast<const int*>(base + ph.fll_beg);
+    const int* ql = reinterpret_cast<const int*>(base + ph.fll_len);
+    const uint32_t* qe = reinterpret_cast<const uint32_t*>(base + ph.fll_ent);
+    for (int gi = 0; gi < ph.n_fll; ++gi) {
+      const FllGroup& g = QG[gi];
+      bad += g.ntgt < 1 || g.ntgt > kFllTargets;
+      for (int m = 0; m < g.ntgt; ++m) {
+        const int i = g.tgt_off + m, t = qt[i];
+        written[t]++;
+        bad += tlevel.count(t) == 0 || tlevel[t] != g.level;
+        bad += m > 0 && ql[i] > ql[i - 1];  // longest first
+        for (int j = 0; j < ql[i]; ++j) {
+          const uint32_t w = qe[qb[i] + j];
+          got[Pair(t, (int)(w >> 9), (int)(w & 511))]++;
+          ++list_pairs;
         }
       }
     }

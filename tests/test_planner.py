@@ -14,7 +14,8 @@ from paper_1911_10228_gb300.inputs import box_coords, config_plain_32, random_sp
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PLANS = [(0, (4, 4, 8)), (30, (4, 4, 8)), (100, (2, 4, 8)), (50, (4, 4, 4)), (30, (8, 4, 4))]
-# FP32 MAC forms: the frequency-lane groups (default) and the parent groups with pair lists
+# FP32 MAC forms (FLGF_CTX_MAC): frequency-lane groups with frequency-lane pair lists (default, 1) or with
+# the shared-memory pair lists (2), and the parent groups with the shared-memory pair lists (0)
 
 
 def _write_mesh(path, N, problems):
@@ -51,12 +52,13 @@ def _meshes():
     }
 
 
-@pytest.mark.parametrize("fp64,mac", [(0, 1), (0, 0), (1, 0)], ids=["fp32-lane", "fp32-groups", "fp64"])
+@pytest.mark.parametrize("fp64,mac", [(0, 1), (0, 2), (0, 0), (1, 0)],
+                         ids=["fp32-lane", "fp32-lane-smemlists", "fp32-groups", "fp64"])
 def test_every_interaction_once_in_the_launch_lists(harness, tmp_path, fp64, mac):
     for name, (N, problems) in _meshes().items():
         mesh = tmp_path / f"{name}.bin"
         _write_mesh(mesh, N, problems)
-        for pct, tile in (PLANS[:2] if mac == 1 else PLANS):
+        for pct, tile in (PLANS[1:3] if mac >= 1 else PLANS):
             out = subprocess.run([str(harness), str(mesh), str(pct), *map(str, tile), str(fp64), str(mac)],
                                  capture_output=True, text=True, timeout=300)
             assert out.returncode == 0 and out.stdout.strip().endswith("ok"), (name, pct, tile, out.stdout)
@@ -71,7 +73,7 @@ def test_vector_groups_cover_every_component(harness, tmp_path):
             continue
         mesh = tmp_path / f"{name}3.bin"
         _write_mesh(mesh, N, problems * 3)
-        for pct, tile in PLANS[:2]:
+        for pct, tile in PLANS[1:3]:
             out = subprocess.run([str(harness), str(mesh), str(pct), *map(str, tile), "0", "1", "3"],
                                  capture_output=True, text=True, timeout=300)
             assert out.returncode == 0 and out.stdout.strip().endswith("ok"), (name, pct, tile, out.stdout)
