@@ -204,6 +204,64 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(N * N)
   cluster.sync();  // no CTA leaves while others still read its shared memory
 }
 
+// a1 for levels with many parents: one CTA per parent walks its existing
+// children in rank order (the same three passes per child) and adds each
+// child's contribution to its running sum in that order, so the parent is
+// bit-identical to the cluster form's, without CTAs for absent children
+// (sparse octrees have three children per parent on average).
+template <typename R, int N, int NI>
+__global__ void __launch_bounds__(N * N) anterp_seq_kernel(const double* __restrict__ J1, const int* __restrict__ parents,
+                                                           const int* __restrict__ children, R* __restrict__ nodes) {
+  constexpr int N3 = N * N * N, PS = N * N * (N + 1);
+  constexpr int V = 16 / (int)sizeof(R);
+  constexpr int PER = N3 / V / (N * N);
+  __shared__ R W[2 * N * NI];
+  __shared__ __align__(16) R A[PS];
+  load_band<R, N, NI>(J1, W);
+  const int t = threadIdx.x, u = t / N, v = t % N;
+  const int pi = blockIdx.x;
+  R tot[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) tot[q] = R(0);
+  for (int c = 0; c < 8; ++c) {
+    const int cid = children[pi * 8 + c];
+    if (cid < 0) continue;  // uniform over the CTA
+    const int c0 = c >> 2, c1 = (c >> 1) & 1, c2 = c & 1;
+    const int4* src = reinterpret_cast<const int4*>(nodes + (size_t)cid * N3);
+    __syncthreads();  // the previous child's last pass has read A
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int4 val = __ldg(src + t + p * N * N);
+      const int i = (t + p * N * N) * V;
+      const R* pv = reinterpret_cast<const R*>(&val);
+#pragma unroll
+      for (int j = 0; j < V; ++j) A[pidx<N>(i / (N * N), (i / N) % N, i % N + j)] = pv[j];
+    }
+    __syncthreads();
+    R in[N], out[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) { in[k] = A[pidx<N>(u, v, k)]; out[k] = R(0); }
+    if (c2) line_anterp<R, N, NI, 1>(in, out, W); else line_anterp<R, N, NI, 0>(in, out, W);
+#pragma unroll
+    for (int k = 0; k < N; ++k) A[pidx<N>(u, v, k)] = out[k];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < N; ++j) { in[j] = A[pidx<N>(u, j, v)]; out[j] = R(0); }
+    if (c1) line_anterp<R, N, NI, 1>(in, out, W); else line_anterp<R, N, NI, 0>(in, out, W);
+#pragma unroll
+    for (int j = 0; j < N; ++j) A[pidx<N>(u, j, v)] = out[j];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) { in[i] = A[pidx<N>(i, u, v)]; out[i] = R(0); }
+    if (c0) line_anterp<R, N, NI, 1>(in, out, W); else line_anterp<R, N, NI, 0>(in, out, W);
+#pragma unroll
+    for (int i = 0; i < N; ++i) tot[i] += out[i];
+  }
+  R* dst = nodes + (size_t)parents[pi] * N3;
+#pragma unroll
+  for (int i = 0; i < N; ++i) dst[(i * N + u) * N + v] = tot[i];
+}
+
 // a5: child += (J_c0 x J_c1 x J_c2) parent, in arithmetic type C: R, or the
 // compensated ff for FP32 data (the three passes then keep their intermediate
 // lines in float-float, so the rounding of one pass is not amplified by the
@@ -531,9 +589,16 @@ static cudaError_t set_smem(Kern k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Levels with at least kAnterpSeqParents parents (enough CTAs to fill the GPU
+// without splitting parents) take one CTA per parent, the others a cluster of
+// 8 CTAs per parent.
+constexpr int kAnterpSeqParents = 2048;
 template <typename R, int N, int NI>
 static cudaError_t anterp_n(const double* J1, const int* parents, const int* children, int n, R* nodes, cudaStream_t s) {
-  anterp_kernel<R, N, NI><<<8 * n, N * N, 0, s>>>(J1, parents, children, nodes);  // clusters of 8 CTAs
+  if (n >= kAnterpSeqParents)
+    anterp_seq_kernel<R, N, NI><<<n, N * N, 0, s>>>(J1, parents, children, nodes);
+  else
+    anterp_kernel<R, N, NI><<<8 * n, N * N, 0, s>>>(J1, parents, children, nodes);  // clusters of 8 CTAs
   return cudaGetLastError();
 }
 template <typename R, int N, int NI>

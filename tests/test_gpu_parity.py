@@ -213,3 +213,22 @@ def test_mesh_errors_are_reported():
         F.BlockSet(c, [[box_coords(3), np.array([[2, 2, 2]])]], [1.0])
     with pytest.raises(F.FLGFError, match="buffer"):
         F.BlockSet(c, [[box_coords(2), box_coords(2)]], [1.0])
+
+
+def test_per_parent_anterpolation_equals_cluster_form():
+    """Octree levels with at least 2048 parents take the one-CTA-per-parent
+    anterpolation, smaller ones the 8-CTA cluster form; both add the children's
+    contributions in rank order, so a batch large enough for the first form
+    equals its problems solved alone (second form) bit for bit."""
+    from paper_1911_10228_gb300.inputs import random_sparse_problem
+    probs = [random_sparse_problem(s, N=8, nblk_range=(400, 900), max_levels=1) for s in range(16)]
+    parents = [len(np.unique(np.asarray(p.coords[0]) >> 1, axis=0)) for p in probs]
+    assert sum(parents) >= 2048 and max(parents) < 2048, parents   # one launch of each form
+    c = ctx(8, "fp32")
+    singles = [F.solve_problem(c, p)[0].cpu() for p in probs]
+    bs = F.BlockSet(c, [p.coords for p in probs], [p.h0 for p in probs])
+    for i, p in enumerate(probs):
+        bs.load_source(i, 0, torch.as_tensor(p.f[0]))
+    bs.solve()
+    for i in range(len(probs)):
+        assert torch.equal(bs.potential(i, 0).cpu(), singles[i]), i
