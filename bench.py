@@ -141,8 +141,9 @@ def file_sha(path):
 
 
 def ncu_traffic(kernel_src: str, kernel: str, workload: str):
-    """DRAM bytes per step of a kernel from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+    """DRAM bytes per step (all launches of one solve) of a kernel from the
+    committed ncu summary, if it was taken on the current kernel source (else
+    None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -153,7 +154,7 @@ def ncu_traffic(kernel_src: str, kernel: str, workload: str):
                 continue
             kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
             if kv.get("kernel") == kernel and kv.get("src_sha") == sha and kv.get("workload") == workload:
-                return float(kv["dram_bytes"])
+                return float(kv["dram_bytes_per_step"])
     return None
 
 
@@ -560,11 +561,11 @@ def run_ours(a, rank, world):
                    "compensated_coarse_levels": True,
                    "parallelism": "independent problems per rank" if world > 1 else "single GPU"},
         "rel_err": {"fp32_vs_fp64_linf": batched.get("fp32_vs_fp64_linf"), **(err or {})},
-        "roofline": {"bound": "alu", "kernel": "spectrum MAC (hadamard_kernel + hadamard_list_kernel), "
+        "roofline": {"bound": "alu", "kernel": "spectrum MAC (hadamard_fl_kernel + hadamard_fll_kernel), "
                                                "all launches of one batched solve",
                      "achieved": mac_tflops, "peak": peak, "unit": "TFLOP/s",
                      "frac": (mac_tflops / peak) if mac_tflops else None,
-                     "traffic": ncu_traffic("hadamard.cu", "hadamard", f"batched{a.problems}"),
+                     "traffic": ncu_traffic("hadamard_fl.cu", "spectrum_mac", f"batched{a.problems}"),
                      "peak_note": f"FP32 FMA: {n_sm} SMs x {FP32_LANES} lanes x 2 flop x {sm_mhz_peak:.0f} MHz",
                      "flops_per_step": mac_flops,
                      "flops_note": "useful (target, source) block pairs x 2N*2N*(N+1) frequencies x 8 flop"},

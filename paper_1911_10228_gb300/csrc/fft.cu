@@ -62,6 +62,24 @@ template <> __device__ __forceinline__ float tw_im<float>(int j) { return c_twf[
 template <> __device__ __forceinline__ ff tw_re<ff>(int j) { return ff(c_twff[j][0], c_twff[j][1]); }
 template <> __device__ __forceinline__ ff tw_im<ff>(int j) { return ff(c_twff[j][2], c_twff[j][3]); }
 
+// (tr, ti) = (wr + i wi)(xr + i xi).  Float-float takes each component as a
+// two-term compensated dot product (DotAcc): one renormalisation instead of
+// three.
+template <typename R>
+__device__ __forceinline__ void twiddle_mul(R wr, R wi, R xr, R xi, R& tr, R& ti) {
+  if constexpr (std::is_same<R, ff>::value) {
+    DotAcc<ff> a = DotAcc<ff>::prod(wr, xr);
+    a.add(-wi, xi);
+    DotAcc<ff> b = DotAcc<ff>::prod(wr, xi);
+    b.add(wi, xr);
+    tr = a.result();
+    ti = b.result();
+  } else {
+    tr = wr * xr - wi * xi;
+    ti = wr * xi + wi * xr;
+  }
+}
+
 // In-register radix-2 FFT of length L (<= 32), natural order in and out.
 // DIR = -1: forward (e^{-2 pi i jk/L}); DIR = +1: inverse without
 // normalisation.  Recursive even/odd split: every array index is a
@@ -89,8 +107,7 @@ struct RegFFT {
       } else {
         const R wr = tw_re<R>(k * (32 / L));
         const R wi = DIR < 0 ? tw_im<R>(k * (32 / L)) : -tw_im<R>(k * (32 / L));
-        tr = wr * odr[k] - wi * odi[k];
-        ti = wr * odi[k] + wi * odr[k];
+        twiddle_mul(wr, wi, odr[k], odi[k], tr, ti);
       }
       re[k] = er[k] + tr; im[k] = ei[k] + ti;
       re[k + H] = er[k] - tr; im[k + H] = ei[k] - ti;
@@ -154,8 +171,15 @@ __device__ __forceinline__ void fft_inv_pruned(const R* Xr, const R* Xi, R* xr, 
   for (int j = 0; j < H; ++j) {
     if (j == 0) { xr[j] = er[j] + odr[j]; xi[j] = ei[j] + odi[j]; continue; }
     const R wr = tw_re<R>(j * (32 / L)), wi = -tw_im<R>(j * (32 / L));
-    xr[j] = er[j] + (odr[j] * wr - odi[j] * wi);
-    xi[j] = ei[j] + (odr[j] * wi + odi[j] * wr);
+    if constexpr (std::is_same<R, ff>::value) {
+      R tr, ti;
+      twiddle_mul(wr, wi, odr[j], odi[j], tr, ti);
+      xr[j] = er[j] + tr;
+      xi[j] = ei[j] + ti;
+    } else {
+      xr[j] = er[j] + (odr[j] * wr - odi[j] * wi);
+      xi[j] = ei[j] + (odr[j] * wi + odi[j] * wr);
+    }
   }
 }
 
@@ -326,9 +350,8 @@ __device__ __forceinline__ void half_line_inverse(int par, C (&hr)[16], C (&hi)[
   if (par) {
 #pragma unroll
     for (int j = 1; j < H; ++j) {
-      const C wr = tw_re<C>(j), wi = -tw_im<C>(j);
-      const C tr = hr[j] * wr - hi[j] * wi;
-      const C ti = hr[j] * wi + hi[j] * wr;
+      C tr, ti;
+      twiddle_mul(tw_re<C>(j), -tw_im<C>(j), hr[j], hi[j], tr, ti);
       hr[j] = tr;
       hi[j] = ti;
     }
@@ -540,12 +563,12 @@ static cudaError_t launch_inv(int N, const cplx<R>* ac, int spec_blocks, const i
       cudaError_t e = set_smem(fft_inv2_kernel<R, 16, C, TH2>, sm);
       if (e != cudaSuccess) return e;
       fft_inv2_kernel<R, 16, C, TH2><<<count, TH2, sm, s>>>(ac, spec_blocks, sids, gids, scales, out);
-      return cudaGetLastError();
+    } else {
+      constexpr int TH = inv_threads<C, 16>();
+      cudaError_t e = set_smem(fft_inv_kernel<R, 16, C, TH>, sm);
+      if (e != cudaSuccess) return e;
+      fft_inv_kernel<R, 16, C, TH><<<count, TH, sm, s>>>(ac, spec_blocks, sids, gids, scales, out);
     }
-    constexpr int TH = inv_threads<C, 16>();
-    cudaError_t e = set_smem(fft_inv_kernel<R, 16, C, TH>, sm);
-    if (e != cudaSuccess) return e;
-    fft_inv_kernel<R, 16, C, TH><<<count, TH, sm, s>>>(ac, spec_blocks, sids, gids, scales, out);
   } else if (N == 8) {
     const size_t sm = sizeof(cplx<C>) * 8 * 16 * 9;
     constexpr int TH = inv_threads<C, 8>();

@@ -70,11 +70,11 @@ __device__ __forceinline__ void line_interp(const R* in, R* out, const R* W) {
     const int s = band_start<N, NI>(j);
     const double t = window_pos<N, NI>(j);
     const double mid = 0.5 * (NI - 1);
-    R acc;
     if (t >= mid - 0.5 && t <= mid + 0.5) {
-      acc = Arith<R>::from_d(0.0);
+      DotAcc<R> acc = DotAcc<R>::zero();
 #pragma unroll
-      for (int m = 0; m < NI; ++m) acc = mad(W[j * NI + m], in[s + m], acc);
+      for (int m = 0; m < NI; ++m) acc.add(W[j * NI + m], in[s + m]);
+      out[r] = acc.result();
     } else if (t < mid) {
       R d[NI];
 #pragma unroll
@@ -83,9 +83,10 @@ __device__ __forceinline__ void line_interp(const R* in, R* out, const R* W) {
       for (int k = 1; k < NI; ++k)
 #pragma unroll
         for (int i = NI - 1; i >= k; --i) d[i] = d[i] - d[i - 1];  // d[k] = forward difference of order k at s
-      acc = d[NI - 1] * Arith<R>::from_d(newton_coef<false>(t, NI - 1));
+      DotAcc<R> acc = DotAcc<R>::prod(d[NI - 1], Arith<R>::from_d(newton_coef<false>(t, NI - 1)));
 #pragma unroll
-      for (int k = NI - 2; k >= 0; --k) acc = mad(Arith<R>::from_d(newton_coef<false>(t, k)), d[k], acc);
+      for (int k = NI - 2; k >= 0; --k) acc.add(Arith<R>::from_d(newton_coef<false>(t, k)), d[k]);
+      out[r] = acc.result();
     } else {
       R d[NI];
 #pragma unroll
@@ -95,11 +96,11 @@ __device__ __forceinline__ void line_interp(const R* in, R* out, const R* W) {
 #pragma unroll
         for (int i = NI - 1; i >= k; --i) d[i] = d[i - 1] - d[i];  // d[k] = backward difference of order k at s + NI - 1
       const double tau = t - (NI - 1);
-      acc = d[NI - 1] * Arith<R>::from_d(newton_coef<true>(tau, NI - 1));
+      DotAcc<R> acc = DotAcc<R>::prod(d[NI - 1], Arith<R>::from_d(newton_coef<true>(tau, NI - 1)));
 #pragma unroll
-      for (int k = NI - 2; k >= 0; --k) acc = mad(Arith<R>::from_d(newton_coef<true>(tau, k)), d[k], acc);
+      for (int k = NI - 2; k >= 0; --k) acc.add(Arith<R>::from_d(newton_coef<true>(tau, k)), d[k]);
+      out[r] = acc.result();
     }
-    out[r] = acc;
   }
 }
 // Its adjoint (anterpolation): out[q] += sum_r J[C N + r][q] in[r].
