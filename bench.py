@@ -67,6 +67,9 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle budget of the cpu_baseline sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the batched solve's kernels one by one instead of replaying its CUDA graph "
+                         "(profiling runs: ncu's replay of the graph's kernel nodes failed to launch the MAC)")
     ap.add_argument("--plan", default=None,
                     help="fixed MAC plan for the batched leg, e.g. 30/4x4x4 (list percentage / tile); default: autotune")
     return ap.parse_args()
@@ -295,7 +298,7 @@ def run_ours(a, rank, world):
         for i, p in enumerate(probs):
             for l, f in enumerate(p.f):
                 bbs.load_source(i, l, torch.as_tensor(f))
-        bbs.set_option(F.OPT_GRAPH, 1)
+        bbs.set_option(F.OPT_GRAPH, 0 if a.no_graph else 1)
         bbs.set_option(F.OPT_TIMING, 1)    # stage events inside the captured graph
         # the FP64 batched solve takes seconds: one warm-up and one step (it also serves the error check)
         for _ in range(max(1, a.warmup) if prec == "fp32" else 1):
@@ -558,7 +561,7 @@ def run_ours(a, rank, world):
         "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD, "problems": len(probs), "N": 16, "n_interp": 6,
                    "dof": int(bdof), "l2": "flushed before every timed step (256 MB write)",
-                   "compensated_coarse_levels": True,
+                   "compensated_coarse_levels": True, "cuda_graph": not a.no_graph,
                    "parallelism": "independent problems per rank" if world > 1 else "single GPU"},
         "rel_err": {"fp32_vs_fp64_linf": batched.get("fp32_vs_fp64_linf"), **(err or {})},
         "roofline": {"bound": "alu", "kernel": "spectrum MAC (hadamard_fl_kernel + hadamard_fll_kernel), "

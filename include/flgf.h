@@ -179,14 +179,14 @@ int flgf_blockset_create_masked(flgf_ctx* ctx, int n_problems, const int* n_leve
  * streamfunction of a vorticity field, each a scalar problem on the same
  * mesh): n_components copies of one mesh (n_levels, nblk[n_levels], coords as
  * for one problem of flgf_blockset_create) as the problems 0 .. n_components-1
- * of one block set, problem c holding component c.  An FP32 block set of
- * three components (FLGF_CTX_MAC = 1) runs the dense spectrum products of
- * all components in one kernel in which each kernel-spectrum read serves the
- * three components' products; the sums are the same, in the same order, as
- * in three independent solves, so each component's potential equals its own
- * scalar solve bit for bit.  Other precisions and component counts solve the
- * components as independent problems of the block set.  1 <= n_components
- * <= 64; arrays are borrowed for the call. */
+ * of one block set, problem c holding component c.  In an FP32 block set
+ * (FLGF_CTX_MAC >= 1) the dense spectrum products of all components run in
+ * the same CTAs, which stage the kernel spectra and the group tables once for
+ * every component; the sums are the same, in the same order, as in
+ * independent solves, so each component's potential equals its own scalar
+ * solve bit for bit.  FP64 block sets solve the components as independent
+ * problems of the block set.  1 <= n_components <= 64; arrays are borrowed
+ * for the call. */
 int flgf_blockset_create_vector(flgf_ctx* ctx, int n_components, int n_levels, const int* nblk,
                                 const int32_t* coords, double h0, flgf_blockset** out);
 void flgf_blockset_destroy(flgf_blockset* bs);

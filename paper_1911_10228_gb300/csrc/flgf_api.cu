@@ -470,9 +470,9 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
   // shared-memory pair-list kernel (mac 0 and 2)
   const bool fll_lists = ctx->prec == FLGF_FP32 && ctx->mac == 1;
   // vector block set (identical meshes, problem c = component c): component
-  // 0's dense tiles serve every component through the component-sharing
-  // kernel, whose columns for component c are component 0's + c * cstride
-  const int vcomp = fl && ncomp == kFlvComponents ? ncomp : 1;
+  // 0's dense tiles serve every component (columns + c * cstride) in the same
+  // CTAs, which stage the kernel spectra and group tables once
+  const int vcomp = fl ? ncomp : 1;
   const int list_pct = ctx->list_pct;
   // interaction tiles of one (instance, octree level): the expensive part of
   // list building, run on the host's cores (see below)
@@ -793,6 +793,23 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
   ph.itp_par.assign(maxtop + 1, 0);
   ph.itp_cpos.assign(maxtop + 1, 0);
   for (int k = 0; k <= maxtop; ++k) {
+    // interpolation children grouped by child position: the CTAs resident on
+    // an SM then take the same one of the kernel's per-axis code paths, which
+    // keeps its instruction working set small (children are independent)
+    {
+      std::vector<int> ord(itp_ch[k].size());
+      for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+      std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return itp_cpos[k][x] < itp_cpos[k][y]; });
+      std::vector<int> ch(ord.size()), par(ord.size()), cp(ord.size());
+      for (size_t i = 0; i < ord.size(); ++i) {
+        ch[i] = itp_ch[k][ord[i]];
+        par[i] = itp_par[k][ord[i]];
+        cp[i] = itp_cpos[k][ord[i]];
+      }
+      itp_ch[k].swap(ch);
+      itp_par[k].swap(par);
+      itp_cpos[k].swap(cp);
+    }
     ph.n_ant[k] = (int)ant_par[k].size();
     ph.ant_par[k] = ar.add(ant_par[k]);
     ph.ant_ch[k] = ar.add(ant_ch[k]);
@@ -1440,16 +1457,10 @@ cudaError_t enqueue_fmm(flgf_blockset* bs, const Arena& ar, const PhaseOff& ph, 
                                        ph.max_units, ar.at<int>(ph.src_ids), ar.at<int>(ph.tgt_ids),
                                        ar.at<uint16_t>(ph.par_tab), bs->spec, bs->acc, ph.nblocks, c->d_kspec,
                                        c->kstride, s));
-    if (ph.fl_ncomp > 1)
-      KRUN(ph.n_fl, launch_hadamard_flv(N, ph.fl_ncomp, ph.fl_cstride, ar.at<FlGroup>(ph.fl_groups), ph.n_fl,
-                                        ph.fl_max_cells, ph.fl_max_parents, ar.at<uint16_t>(ph.fl_rows),
-                                        ar.at<uint32_t>(ph.fl_dlms), ar.at<int>(ph.fl_tgt), ar.at<int>(ph.fl_cells), bs->spec, bs->acc,
-                                        ph.nblocks, c->d_kspec, c->kstride, s));
-    else
-      KRUN(ph.n_fl, launch_hadamard_fl(N, ar.at<FlGroup>(ph.fl_groups), ph.n_fl, ph.fl_max_cells, ph.fl_max_parents,
-                                       ar.at<uint16_t>(ph.fl_rows), ar.at<uint32_t>(ph.fl_dlms), ar.at<int>(ph.fl_tgt),
-                                       ar.at<int>(ph.fl_cells),
-                                       bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));
+    KRUN(ph.n_fl, launch_hadamard_fl(N, ar.at<FlGroup>(ph.fl_groups), ph.n_fl, ph.fl_max_cells, ph.fl_max_parents,
+                                     ar.at<uint16_t>(ph.fl_rows), ar.at<uint32_t>(ph.fl_dlms), ar.at<int>(ph.fl_tgt),
+                                     ar.at<int>(ph.fl_cells), bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride,
+                                     ph.fl_ncomp, ph.fl_cstride, s));
     KRUN(ph.n_fll, launch_hadamard_fll(N, ar.at<FllGroup>(ph.fll_groups), ph.n_fll, ar.at<int>(ph.fll_tgt),
                                        ar.at<int>(ph.fll_beg), ar.at<int>(ph.fll_len), ar.at<uint32_t>(ph.fll_ent),
                                        bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));

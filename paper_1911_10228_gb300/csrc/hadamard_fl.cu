@@ -128,11 +128,14 @@ __device__ __forceinline__ const float4* kernel_row(const float4* Ks, int w, int
 
 }  // namespace
 
+// kVec: a vector block set (ncomp components); the scalar form compiles
+// without the component loop.
+template <bool kVec>
 __global__ void __launch_bounds__(kFlThreads, 1)
     hadamard_fl_kernel(const FlGroup* __restrict__ groups, int ngroups, const uint16_t* __restrict__ rows,
                        const uint32_t* __restrict__ dlms, const int* __restrict__ tgt_ids, const int* __restrict__ cells,
                        const float2* __restrict__ spec, float2* __restrict__ acc, int spec_blocks,
-                       const float2* __restrict__ kspec, size_t kstride) {
+                       const float2* __restrict__ kspec, size_t kstride, int ncomp, int cstride) {
   constexpr int T = ChunkT<float>::value;  // 4 frequencies per chunk
   constexpr int CPB = kFlFreq / T;         // 16 chunks per frequency block
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -168,9 +171,13 @@ __global__ void __launch_bounds__(kFlThreads, 1)
 
   const int lane = tid & 31, warp = tid >> 5;
   const int chunk = chunk0 + (2 * lane) / T, t = (2 * lane) % T;  // this lane's two frequencies (t even)
-  const float2* lane_spec = spec + chunk_offset<float>(chunk, 0, spec_blocks) + t;
-  float2* lane_acc = acc + chunk_offset<float>(chunk, 0, spec_blocks) + t;
   const float4* Ks4 = reinterpret_cast<const float4*>(Ks);
+  // components of a vector block set: the same groups at columns + c cstride,
+  // against the kernel spectra and tables staged once
+  for (int comp = 0; comp < (kVec ? ncomp : 1); ++comp) {
+  const size_t coff = (size_t)comp * cstride * (kChunkGroup * T);
+  const float2* lane_spec = spec + chunk_offset<float>(chunk, 0, spec_blocks) + t + coff;
+  float2* lane_acc = acc + chunk_offset<float>(chunk, 0, spec_blocks) + t + coff;
   for (int pm = warp; pm < gp.nact; pm += kFlWarps) {
     const uint16_t* row = PR + pm * kFlRowStride;
     const uint32_t* dm = DM + pm * kFlDelta;
@@ -197,194 +204,58 @@ __global__ void __launch_bounds__(kFlThreads, 1)
           make_float4(ar[a][0], ai[a][0], ar[a][1], ai[a][1]);
     }
   }
+  }
 }
 
-// ---------------------------------------------------------------------------
-// Vector problems (several components on one mesh, e.g. the three Cartesian
-// components of a streamfunction, Sec. 3.1): a warp owns one parent for all
-// NC components, one frequency per lane (K^ rows of 32 frequencies, 88 KB),
-// so every kernel-spectrum read of a (parent, cell) serves the products of
-// every component.  Component c's spectrum columns are component 0's plus
-// c * cstride (the components' blocks are laid out alike).  Per component and
-// frequency the sums run in the same order as in the scalar kernel.
-// ---------------------------------------------------------------------------
 namespace {
-
-constexpr int kFlvWarps = 8;
-constexpr int kFlvThreads = 32 * kFlvWarps;
-constexpr int kFlvFreq = 32;
-
 __device__ __forceinline__ void cmac1(float& ar, float& ai, float2 k, float2 f) {
   ar = fmaf(k.x, f.x, ar);
   ar = fmaf(-k.y, f.y, ar);
   ai = fmaf(k.x, f.y, ai);
   ai = fmaf(k.y, f.x, ai);
 }
-
-__device__ __forceinline__ float2 ld_cg_f2_if(const float2* p, int sid) {
-  float2 v = make_float2(0.f, 0.f);
-  asm volatile("{\n\t.reg .pred q;\n\tsetp.ge.s32 q, %3, 0;\n\t@q ld.global.cg.v2.f32 {%0, %1}, [%2];\n\t}"
-               : "+f"(v.x), "+f"(v.y)
-               : "l"(p), "r"(sid));
-  return v;
-}
-
-template <int NC>
-__device__ __forceinline__ void load_cell_v(const int* cid, const float2* __restrict__ lane_spec, int cstride,
-                                            float2 (&f)[NC][8]) {
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const int sid = cid[b];
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-      f[c][b] = ld_cg_f2_if(lane_spec + (size_t)(max(sid, 0) + c * cstride) * (kChunkGroup * ChunkT<float>::value),
-                            sid);
-  }
-}
-
-template <int NC, bool kAll>
-__device__ __forceinline__ void cell_products_vm(const float2* __restrict__ Kc, uint32_t dlm, const float2 (&f)[NC][8],
-                                                 float (&ar)[NC][8], float (&ai)[NC][8]) {
-#pragma unroll
-  for (int dl = 0; dl < 27; ++dl) {
-    if (!kAll && !((dlm >> dl) & 1u)) continue;
-    const int l0 = dl / 9 - 1, l1 = (dl / 3) % 3 - 1, l2 = dl % 3 - 1;
-    const float2 k = Kc[(l0 * 49 + l1 * 7 + l2) * kFlvFreq];
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int b0 = (a >> 2) - l0, b1 = ((a >> 1) & 1) - l1, b2 = (a & 1) - l2;
-      if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b2 < 0 || b2 > 1) continue;
-      const int b = (b0 << 2) | (b1 << 1) | b2;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) cmac1(ar[c][a], ai[c][a], k, f[c][b]);
-    }
-  }
-}
-template <int NC>
-__device__ __forceinline__ void cell_products_v(const float2* __restrict__ Kc, uint32_t dlm, const float2 (&f)[NC][8],
-                                                float (&ar)[NC][8], float (&ai)[NC][8]) {
-  if (dlm >> 31)
-    cell_products_vm<NC, true>(Kc, dlm, f, ar, ai);
-  else
-    cell_products_vm<NC, false>(Kc, dlm, f, ar, ai);
-}
-
 }  // namespace
-
-template <int NC>
-__global__ void __launch_bounds__(kFlvThreads, 1)
-    hadamard_flv_kernel(const FlGroup* __restrict__ groups, int ngroups, const uint16_t* __restrict__ rows,
-                        const uint32_t* __restrict__ dlms, const int* __restrict__ tgt_ids, const int* __restrict__ cells, int cstride,
-                        const float2* __restrict__ spec, float2* __restrict__ acc, int spec_blocks,
-                        const float2* __restrict__ kspec, size_t kstride) {
-  constexpr int T = ChunkT<float>::value;
-  constexpr int CPB = kFlvFreq / T;  // 8 chunks per frequency block
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* Ks = reinterpret_cast<float2*>(smem_raw);  // [343][32]
-  const int id = blockIdx.x;
-  const int g = id % ngroups, fb = id / ngroups;
-  const FlGroup gp = groups[g];
-  int* CI = reinterpret_cast<int*>(Ks + kNOff * kFlvFreq);
-  int* TG = CI + gp.ncell * 8;
-  uint32_t* DM = reinterpret_cast<uint32_t*>(TG + gp.nact * 8);
-  uint16_t* PR = reinterpret_cast<uint16_t*>(DM + gp.nact * kFlDelta);
-  const int tid = threadIdx.x;
-  const int chunk0 = fb * CPB;
-  {
-    const int4* src = reinterpret_cast<const int4*>(kspec + (size_t)gp.level * kstride + (size_t)chunk0 * kNOff * T);
-    constexpr int NV = CPB * kNOff * T / 2;
-    for (int i = tid; i < NV; i += kFlvThreads) {
-      const int4 v = __ldg(src + i);
-      const int idx = 2 * i;
-      const int c = idx / (kNOff * T), r = idx % (kNOff * T), d = r / T, t = r % T;
-      float2* dst = Ks + d * kFlvFreq + c * T + t;
-      dst[0] = make_float2(__int_as_float(v.x), __int_as_float(v.y));
-      dst[1] = make_float2(__int_as_float(v.z), __int_as_float(v.w));
-    }
-  }
-  for (int i = tid; i < gp.ncell * 8; i += kFlvThreads) CI[i] = __ldg(cells + (size_t)gp.cell_off * 8 + i);
-  for (int i = tid; i < gp.nact * 8; i += kFlvThreads) TG[i] = __ldg(tgt_ids + (size_t)gp.row_off * 8 + i);
-  for (int i = tid; i < gp.nact * kFlDelta; i += kFlvThreads) DM[i] = __ldg(dlms + (size_t)gp.row_off * kFlDelta + i);
-  for (int i = tid; i < gp.nact * kFlRowStride; i += kFlvThreads)
-    PR[i] = __ldg(rows + (size_t)gp.row_off * kFlRowStride + i);
-  __syncthreads();
-
-  const int lane = tid & 31, warp = tid >> 5;
-  const int chunk = chunk0 + lane / T, t = lane % T;
-  const float2* lane_spec = spec + chunk_offset<float>(chunk, 0, spec_blocks) + t;
-  float2* lane_acc = acc + chunk_offset<float>(chunk, 0, spec_blocks) + t;
-  for (int pm = warp; pm < gp.nact; pm += kFlvWarps) {
-    const uint16_t* row = PR + pm * kFlRowStride;
-    const uint32_t* dm = DM + pm * kFlDelta;
-    const int* tg = TG + pm * 8;
-    const int ncl = row[0];
-    float ar[NC][8], ai[NC][8];
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-      for (int a = 0; a < 8; ++a) { ar[c][a] = 0.f; ai[c][a] = 0.f; }
-    float2 fa[NC][8], fb[NC][8];
-    if (ncl > 0) load_cell_v<NC>(CI + 8 * (row[1] & 0x7FF), lane_spec, cstride, fa);
-    for (int j = 0; j < ncl; j += 2) {
-      if (j + 1 < ncl) load_cell_v<NC>(CI + 8 * (row[2 + j] & 0x7FF), lane_spec, cstride, fb);
-      {
-        const int e = row[1 + j] >> 11;
-        cell_products_v<NC>(Ks + off_index(-2 * (e / 9 - 1), -2 * ((e / 3) % 3 - 1), -2 * (e % 3 - 1)) * kFlvFreq + lane,
-                            dm[j], fa, ar, ai);
-      }
-      if (j + 1 >= ncl) break;
-      if (j + 2 < ncl) load_cell_v<NC>(CI + 8 * (row[3 + j] & 0x7FF), lane_spec, cstride, fa);
-      {
-        const int e = row[2 + j] >> 11;
-        cell_products_v<NC>(Ks + off_index(-2 * (e / 9 - 1), -2 * ((e / 3) % 3 - 1), -2 * (e % 3 - 1)) * kFlvFreq + lane,
-                            dm[j + 1], fb, ar, ai);
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      if (tg[a] < 0) continue;
-#pragma unroll
-      for (int c = 0; c < NC; ++c)
-        lane_acc[(size_t)(tg[a] + c * cstride) * (kChunkGroup * T)] = make_float2(ar[c][a], ai[c][a]);
-    }
-  }
-}
-
-cudaError_t launch_hadamard_flv(int N, int ncomp, int cstride, const FlGroup* groups, int ngroups, int max_cells,
-                                int max_parents, const uint16_t* rows, const uint32_t* dlms, const int* tgt_ids,
-                                const int* cells, const void* spec, void* acc, int spec_blocks, const void* kspec,
-                                size_t kspec_level_stride, cudaStream_t s) {
-  if (ngroups <= 0) return cudaSuccess;
-  if (ncomp != kFlvComponents) return cudaErrorInvalidValue;  // the one instantiation
-  const int nfb = nfreq(N) / kFlvFreq;
-  const size_t sm = sizeof(float2) * (size_t)kNOff * kFlvFreq + fl_table_bytes(max_cells, max_parents);
-  if (sm > kFlSmemBytes || (size_t)nfb * ngroups >= (1u << 31)) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(hadamard_flv_kernel<kFlvComponents>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  hadamard_flv_kernel<kFlvComponents><<<(unsigned)(nfb * ngroups), kFlvThreads, sm, s>>>(
-      groups, ngroups, rows, dlms, tgt_ids, cells, cstride, reinterpret_cast<const float2*>(spec),
-      reinterpret_cast<float2*>(acc), spec_blocks, reinterpret_cast<const float2*>(kspec), kspec_level_stride);
-  return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // Pair lists in frequency lanes (the targets of sparse tiles, where few of a
 // parent's 8 x 8 child pairs exist): a warp owns one target block and walks
 // its (source, kernel offset) list; each lane holds one frequency of the
 // CTA's 32-frequency block.  The list is read 32 entries at a time, one per
-// lane, and broadcast by shuffles; eight source loads are in flight before
-// their products.  The kernel spectra of the block ([343][32], 88 KB) sit in
-// shared memory, the sources come through L1 (the group's targets are
-// spatially close and share most of them).  Per pair a lane reads 8 bytes of
-// source and 8 of kernel for 4 FMAs: the unified L1/shared-memory data path
-// bounds the kernel near a quarter of the FMA rate, against one eighth for
-// the shared-memory pair-list kernel.  The products of a target run in list
-// order into two accumulators (even and odd list positions of each batch of
-// eight), summed at the end.
+// lane, and broadcast by shuffles; eight source loads per warp are in flight
+// before their products (sixteen, with 24 warps per CTA, measured 1 % slower
+// on the batch, and so did L2 prefetches of the next entries' sources).  The
+// kernel spectra of the block ([343][32], 88 KB) sit in shared
+// memory, the sources come through L1 (the group's targets are spatially
+// close and share most of them).  Per pair a lane reads 8 bytes of source and
+// 8 of kernel for 4 FMAs: the unified L1/shared-memory data path bounds the
+// kernel near a quarter of the FMA rate, against one eighth for the
+// shared-memory pair-list kernel.  The products of a target run in list order
+// into two accumulators (even and odd list positions), summed at the end.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kFllThreads = 32 * kFllWarps;
+constexpr int kFllBatch = 8;  // source loads in flight per warp
 }  // namespace
+
+// U consecutive list entries of the lane-held batch starting at jj: U source
+// loads in flight, then their products into the even / odd accumulators.
+template <int U>
+__device__ __forceinline__ void fll_batch(uint32_t my, int jj, const float2* __restrict__ lane_spec,
+                                          const float2* __restrict__ Kl, float& ar0, float& ai0, float& ar1,
+                                          float& ai1) {
+  constexpr size_t kCol = kChunkGroup * ChunkT<float>::value;
+  uint32_t e[U];
+  float2 f[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) e[u] = __shfl_sync(0xffffffffu, my, jj + u);
+#pragma unroll
+  for (int u = 0; u < U; ++u) f[u] = __ldg(lane_spec + (size_t)(e[u] >> 9) * kCol);
+#pragma unroll
+  for (int u = 0; u < U; u += 2) {
+    cmac1(ar0, ai0, Kl[(e[u] & 511u) * kFllFreq], f[u]);
+    cmac1(ar1, ai1, Kl[(e[u + 1] & 511u) * kFllFreq], f[u + 1]);
+  }
+}
 
 __global__ void __launch_bounds__(kFllThreads, 1)
     hadamard_fll_kernel(const FllGroup* __restrict__ groups, int ngroups, const int* __restrict__ tgt,
@@ -427,19 +298,8 @@ __global__ void __launch_bounds__(kFllThreads, 1)
       const uint32_t my = j0 + lane < n ? __ldg(ent + b0 + j0 + lane) : 0u;
       const int cnt = min(32, n - j0);
       int jj = 0;
-      for (; jj + 8 <= cnt; jj += 8) {
-        uint32_t e[8];
-        float2 f[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) e[u] = __shfl_sync(0xffffffffu, my, jj + u);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) f[u] = __ldg(lane_spec + (size_t)(e[u] >> 9) * kCol);
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-          cmac1(ar0, ai0, Kl[(e[u] & 511u) * kFllFreq], f[u]);
-          cmac1(ar1, ai1, Kl[(e[u + 1] & 511u) * kFllFreq], f[u + 1]);
-        }
-      }
+      for (; jj + kFllBatch <= cnt; jj += kFllBatch)
+        fll_batch<kFllBatch>(my, jj, lane_spec, Kl, ar0, ai0, ar1, ai1);
       for (; jj < cnt; ++jj) {
         const uint32_t e = __shfl_sync(0xffffffffu, my, jj);
         cmac1(ar0, ai0, Kl[(e & 511u) * kFllFreq], __ldg(lane_spec + (size_t)(e >> 9) * kCol));
@@ -471,16 +331,18 @@ size_t fl_smem_bytes(int max_cells, int max_parents) {
 cudaError_t launch_hadamard_fl(int N, const FlGroup* groups, int ngroups, int max_cells, int max_parents,
                                const uint16_t* rows, const uint32_t* dlms, const int* tgt_ids, const int* cells,
                                const void* spec, void* acc, int spec_blocks, const void* kspec,
-                               size_t kspec_level_stride, cudaStream_t s) {
+                               size_t kspec_level_stride, int ncomp, int cstride, cudaStream_t s) {
   if (ngroups <= 0) return cudaSuccess;
+  if (ncomp < 1) return cudaErrorInvalidValue;
   const int nfb = nfreq(N) / kFlFreq;
   const size_t sm = fl_smem_bytes(max_cells, max_parents);
   if (sm > kFlSmemBytes || (size_t)nfb * ngroups >= (1u << 31)) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(hadamard_fl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  auto kern = ncomp > 1 ? hadamard_fl_kernel<true> : hadamard_fl_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  hadamard_fl_kernel<<<(unsigned)(nfb * ngroups), kFlThreads, sm, s>>>(
+  kern<<<(unsigned)(nfb * ngroups), kFlThreads, sm, s>>>(
       groups, ngroups, rows, dlms, tgt_ids, cells, reinterpret_cast<const float2*>(spec), reinterpret_cast<float2*>(acc),
-      spec_blocks, reinterpret_cast<const float2*>(kspec), kspec_level_stride);
+      spec_blocks, reinterpret_cast<const float2*>(kspec), kspec_level_stride, ncomp, cstride);
   return cudaGetLastError();
 }
 

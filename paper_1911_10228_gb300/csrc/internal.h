@@ -165,10 +165,12 @@ struct FlLists {
 void pack_fl_groups(int level, const std::vector<ParentRec>& recs, FlLists& L);
 uint32_t fl_delta_mask(int level, int e, const int* tgt, const int* src);
 size_t fl_smem_bytes(int max_cells, int max_parents);
+// ncomp > 1: a vector block set's components, whose spectrum columns are
+// component 0's + c * cstride, run through the same groups in one launch.
 cudaError_t launch_hadamard_fl(int N, const FlGroup* groups, int ngroups, int max_cells, int max_parents,
                                const uint16_t* rows, const uint32_t* dlms, const int* tgt_ids, const int* cells,
                                const void* spec, void* acc, int spec_blocks, const void* kspec,
-                               size_t kspec_level_stride, cudaStream_t s);
+                               size_t kspec_level_stride, int ncomp, int cstride, cudaStream_t s);
 // FP32 frequency-lane pair lists (hadamard_fl.cu), for the targets of sparse
 // tiles: a CTA takes a group of at most kFllTargets targets and a block of
 // kFllFreq consecutive frequencies, a warp one target at a time, a lane one
@@ -193,13 +195,7 @@ void pack_fll_groups(int level, const std::vector<std::pair<int, std::vector<int
 cudaError_t launch_hadamard_fll(int N, const FllGroup* groups, int ngroups, const int* tgt, const int* beg,
                                 const int* len, const uint32_t* ent, const void* spec, void* acc, int spec_blocks,
                                 const void* kspec, size_t kspec_level_stride, cudaStream_t s);
-// The component-sharing form for vector block sets of kFlvComponents
-// components: the same groups, component c's spectrum columns at + c * cstride.
-constexpr int kFlvComponents = 3;
-cudaError_t launch_hadamard_flv(int N, int ncomp, int cstride, const FlGroup* groups, int ngroups, int max_cells,
-                                int max_parents, const uint16_t* rows, const uint32_t* dlms, const int* tgt_ids,
-                                const int* cells, const void* spec, void* acc, int spec_blocks, const void* kspec,
-                                size_t kspec_level_stride, cudaStream_t s);
+
 
 // ---- a1/a5 and multi-resolution stencils (stencil.cu) ----------------------
 // J1: dense 1-D Lagrange matrix [2N][N] (row = child node of the two children, column = parent node).
