@@ -270,6 +270,7 @@ def run_ours(a, rank, world):
     def fp32_alu_peak():
         return n_sm * FP32_LANES * 2 * sm_mhz_peak * 1e6 / 1e12
 
+    torch.cuda.nvtx.range_push("batched")  # one NVTX range per leg (profilers select a leg by it)
     # ------------------------------------------------------------------ batched
     seeds = MR.problem_seeds(a.problems, rank)
     probs = config_batched(a.problems, first_seed=seeds[0])
@@ -333,6 +334,8 @@ def run_ours(a, rank, world):
         batched["fp64"] = {k: v for k, v in r64.items() if k != "work"}
         batched["fp32_over_fp64"] = r32["value"] / r64["value"]
 
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("uniform")  # one NVTX range per leg (profilers select a leg by it)
     # ------------------------------------------------------------------ uniform 256^3
     uniform = None
     if "uniform" in legs:
@@ -373,6 +376,8 @@ def run_ours(a, rank, world):
             bs.close()
             ctx.close()
 
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("multires")  # one NVTX range per leg (profilers select a leg by it)
     # ------------------------------------------------------------------ refined torus
     multires = None
     if "multires" in legs:
@@ -407,6 +412,8 @@ def run_ours(a, rank, world):
                                                                     [tp])
         del touts
 
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("adjoint")  # one NVTX range per leg (profilers select a leg by it)
     # ------------------------------------------------------------------ adjoint
     adjoint = None
     if "adjoint" in legs:
@@ -431,6 +438,8 @@ def run_ours(a, rank, world):
         abs_.close()
         actx.close()
 
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("vector")  # one NVTX range per leg (profilers select a leg by it)
     # ------------------------------------------------------------------ vector (three components, one mesh)
     vector = None
     if "vector" in legs:
@@ -466,6 +475,8 @@ def run_ours(a, rank, world):
         vector["mac_ms_over_3_scalar"] = vector["vector3"]["spectrum_mac_ms"] / (3 * vector["scalar1"]["spectrum_mac_ms"])
         vector["solve_ms_over_3_scalar"] = vector["vector3"]["ms_per_step"] / (3 * vector["scalar1"]["ms_per_step"])
 
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("e2e")  # one NVTX range per leg (profilers select a leg by it)
     # ------------------------------------------------------------------ end to end (batched, host buffers)
     e2e = None
     if not a.no_e2e:
@@ -509,6 +520,7 @@ def run_ours(a, rank, world):
                "note": "pinned host buffers through the C ABI (flgf_load_source / flgf_get_potential with host "
                        "pointers); the next step's loads overlap the current solve"}
 
+    torch.cuda.nvtx.range_pop()
     # ------------------------------------------------------------------ CPU oracle baseline and errors
     cpu, err = None, None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
