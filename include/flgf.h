@@ -216,6 +216,27 @@ int flgf_solve(flgf_blockset* bs);
  * missing halo block); the flag is cleared at the start of every solve. */
 int flgf_get_potential(flgf_blockset* bs, int problem, int level, void* u, int where);
 
+/* One step of mesh generation on the device (Sec. 3.1, Eq. ref_crit: a block
+ * of level l is refined where its source exceeds alpha^(L_R - l) times the
+ * largest |source| on the level; Sec. 3: every refined block needs its 26
+ * same-level neighbours).  Inputs on the device: f, the level's source
+ * ([nblk][N][N][N], context precision), and coords ([nblk][3] int32 block
+ * coordinates, |c| < 2^19); rel = alpha^(L_R - l) >= 0.  Outputs on the device:
+ * flags[nblk] = 1 where max over the block of |f| > rel * (max over the level
+ * of |f|), compared in FP64 (all 0 when the level's source is zero);
+ * children[8 nblk][3] = the children (2c + {0,1}^3) of the flagged blocks, the
+ * next level; buffer[26 nblk][3] = the 26-neighbours of flagged blocks that
+ * are not blocks of the level, each once.  Both lists are in Morton order: by
+ * the key interleaving the bits of (x, y, z) + 2^20 (bit i of x at key bit
+ * 3i + 2, of y at 3i + 1, of z at 3i).  counts (host): {children, buffer}.
+ * The call allocates its scratch (about 560 bytes per block) for its duration
+ * and synchronises the context stream.  FLGF_EINVAL for a bad argument, a
+ * coordinate out of range or nblk > 645277; FLGF_ENOMEM when the scratch
+ * cannot be allocated.  The octree and interaction lists are still built on
+ * the host by flgf_blockset_create. */
+int flgf_refine_level(flgf_ctx* ctx, const void* f, int nblk, const int32_t* coords, double rel, uint8_t* flags,
+                      int32_t* children, int32_t* buffer, int* counts);
+
 /* out = L_Q^{(h_l)} u on the blocks of (problem, level), using same-level face
  * neighbours; cells with a missing neighbour get 0 (Sec. 3.1's consistency
  * check omega_h = L_Q Psi_h).  u and out: [nblk][N][N][N]. */

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libflgf.so")
-SOURCES = ["flgf_api.cu", "lgf.cu", "fft.cu", "hadamard.cu", "hadamard_fl.cu", "stencil.cu", "flgf_static.cu"]
+SOURCES = ["flgf_api.cu", "lgf.cu", "fft.cu", "hadamard.cu", "hadamard_fl.cu", "stencil.cu", "flgf_static.cu", "meshgen.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                 "-I" + os.path.join(ROOT, "include")]

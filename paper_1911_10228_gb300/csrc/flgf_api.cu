@@ -1856,6 +1856,21 @@ extern "C" int flgf_laplacian(flgf_blockset* bs, int problem, int level, const v
   return FLGF_OK;
 }
 
+extern "C" int flgf_refine_level(flgf_ctx* ctx, const void* f, int nblk, const int32_t* coords, double rel,
+                                 uint8_t* flags, int32_t* children, int32_t* buffer, int* counts) {
+  if (!ctx || !f || !coords || !flags || !children || !buffer || !counts || nblk < 1 || !(rel >= 0.0) ||
+      rel > 1e300)
+    return fail(ctx, FLGF_EINVAL, "refine_level: bad arguments");
+  counts[0] = counts[1] = 0;
+  const cudaError_t e = launch_refine_level(ctx->N, ctx->prec == FLGF_FP64, f, nblk, coords, rel, flags, children,
+                                            buffer, counts, ctx->stream);
+  if (e == cudaErrorInvalidValue)
+    return fail(ctx, FLGF_EINVAL, "refine_level: a coordinate outside (-2^19, 2^19) or more than 645277 blocks");
+  if (e == cudaErrorMemoryAllocation) return fail(ctx, FLGF_ENOMEM, "refine_level: scratch allocation");
+  if (e != cudaSuccess) return fail(ctx, FLGF_ECUDA, std::string("refine_level: ") + cudaGetErrorString(e));
+  return FLGF_OK;
+}
+
 // ----------------------------------------------------------------------------
 // Read-only view of a context for other translation units of the library.
 // ----------------------------------------------------------------------------

@@ -197,6 +197,13 @@ cudaError_t launch_hadamard_fll(int N, const FllGroup* groups, int ngroups, cons
                                 const void* kspec, size_t kspec_level_stride, cudaStream_t s);
 
 
+// ---- on-device refinement of a level (meshgen.cu) ----------------------------
+// f: [nblk][N^3] in the context precision; coords, flags, children, buffer on
+// the device, counts on the host (see flgf_refine_level).  cudaErrorInvalidValue
+// for a coordinate outside (-2^19, 2^19) or more than 2^24 / 26 blocks.
+cudaError_t launch_refine_level(int N, int prec_fp64, const void* f, int nblk, const int32_t* coords, double rel,
+                                uint8_t* flags, int32_t* children, int32_t* buffer, int* counts, cudaStream_t s);
+
 // ---- a1/a5 and multi-resolution stencils (stencil.cu) ----------------------
 // J1: dense 1-D Lagrange matrix [2N][N] (row = child node of the two children, column = parent node).
 template <typename R>

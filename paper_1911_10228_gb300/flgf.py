@@ -79,6 +79,8 @@ PROTOTYPES = {
     "flgf_load_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
     "flgf_solve_adjoint": (ctypes.c_int, [ctypes.c_void_p]),
     "flgf_get_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    "flgf_refine_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "flgf_convolve_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_i32_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_double]),
 }
@@ -195,6 +197,28 @@ class Context:
         torch.cuda.current_stream(self.device).wait_stream(self.stream)
         f.record_stream(self.stream)
         return out
+
+    def refine_level(self, f: torch.Tensor, coords, rel: float):
+        """One refinement step on the device (flgf_refine_level, Eq. ref_crit):
+        f (nblk, N, N, N) the level's source, coords (nblk, 3) its block
+        coordinates, rel = alpha^(L_R - l).  Returns device tensors (flags (nblk,)
+        bool, children (m, 3) int32, buffer (k, 3) int32), the lists in Morton order."""
+        coords = torch.as_tensor(coords, dtype=torch.int32).reshape(-1, 3).to(self.device).contiguous()
+        n = coords.shape[0]
+        shape = (n, self.N, self.N, self.N)
+        if not isinstance(f, torch.Tensor) or tuple(f.shape) != shape:
+            raise ValueError(f"f must be a tensor of shape {shape}")
+        f = f.to(device=self.device, dtype=self.dtype).contiguous()
+        flags = torch.empty(n, dtype=torch.uint8, device=self.device)
+        children = torch.empty((8 * n, 3), dtype=torch.int32, device=self.device)
+        buffer = torch.empty((26 * n, 3), dtype=torch.int32, device=self.device)
+        counts = (ctypes.c_int * 2)()
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self.check(self.lib.flgf_refine_level(self.handle, ctypes.c_void_p(f.data_ptr()), n,
+                                              ctypes.c_void_p(coords.data_ptr()), float(rel),
+                                              ctypes.c_void_p(flags.data_ptr()), ctypes.c_void_p(children.data_ptr()),
+                                              ctypes.c_void_p(buffer.data_ptr()), counts), "flgf_refine_level")
+        return flags.bool(), children[:counts[0]], buffer[:counts[1]]
 
     def close(self):
         if getattr(self, "handle", None):
