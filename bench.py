@@ -61,7 +61,7 @@ def args_parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--problems", type=int, default=64, help="problems of the batched workload per GPU")
-    ap.add_argument("--legs", default="batched,uniform,multires,adjoint,vector",
+    ap.add_argument("--legs", default="batched,uniform,multires,adjoint,vector,meshgen",
                     help="legs to run; the batched leg (the headline) always runs")
     ap.add_argument("--precisions", default="fp32,fp64", help="contexts to time (profiling runs use fp32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -295,7 +295,10 @@ def run_ours(a, rank, world):
                                "ms_per_solve": {f"{k[0]}/{'x'.join(map(str, k[1]))}": round(v, 2)
                                                 for k, v in table.items()}}
         bctx.set_plan(list_pct=plan[0], tile=plan[1])
+        t_create = time.time()
         bbs = F.BlockSet(bctx, [p.coords for p in probs], [p.h0 for p in probs])
+        torch.cuda.synchronize()
+        t_create = time.time() - t_create   # host planner (octrees, lists, groups) and device allocation
         for i, p in enumerate(probs):
             for l, f in enumerate(p.f):
                 bbs.load_source(i, l, torch.as_tensor(f))
@@ -310,6 +313,7 @@ def run_ours(a, rank, world):
         ms = timed(bctx.stream, bbs.solve, nb)
         stage, n_timed = bbs.stage_times(reset=True)
         res[prec] = {"value": bdof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "steps": nb,
+                     "blockset_create_s": t_create,
                      "launches_per_step": bbs.launch_count(),
                      "stages_ms": {k: v / max(n_timed, 1) for k, v in stage.items()},
                      "work": bbs.work_counts()}
@@ -376,6 +380,29 @@ def run_ours(a, rank, world):
             bs.close()
             ctx.close()
 
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("meshgen")  # one NVTX range per leg (profilers select a leg by it)
+    # ------------------------------------------------------------------ on-device refinement step
+    meshgen = None
+    if "meshgen" in legs:
+        from paper_1911_10228_gb300.inputs import config_uniform_256
+        mp = config_uniform_256()
+        mctx = F.Context(N=16, n_interp=6, precision="fp32")
+        mf = torch.as_tensor(mp.f[0]).to("cuda", torch.float32)
+        mc = torch.as_tensor(mp.coords[0], dtype=torch.int32).cuda()
+        flags, ch, buf = mctx.refine_level(mf, mc, 1e-3)   # warm-up
+        torch.cuda.synchronize()
+        reps = 5
+        t0 = time.time()
+        for _ in range(reps):
+            flags, ch, buf = mctx.refine_level(mf, mc, 1e-3)
+        torch.cuda.synchronize()
+        meshgen = {"workload": "refinement step (Eq. ref_crit, rel 1e-3) of the 256^3 lattice's 4096 blocks of 16^3: "
+                               "flags, Morton-sorted children and 26-neighbour buffer on the device",
+                   "ms_per_call": (time.time() - t0) / reps * 1e3, "refined": int(flags.sum()),
+                   "children": int(ch.shape[0]), "buffer": int(buf.shape[0]),
+                   "note": "wall clock: the call synchronises (it returns the list lengths to the host)"}
+        mctx.close()
     torch.cuda.nvtx.range_pop()
     torch.cuda.nvtx.range_push("multires")  # one NVTX range per leg (profilers select a leg by it)
     # ------------------------------------------------------------------ refined torus
@@ -590,6 +617,7 @@ def run_ours(a, rank, world):
         "multires": multires,
         "adjoint": adjoint,
         "vector": vector,
+        "meshgen": meshgen,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": r32["launches_per_step"] * a.steps,

@@ -81,3 +81,73 @@ def test_vortex_ring_added_levels_and_correction():
     assert fine[(3, True)] / fine[(4, True)] > 3 and fine[(4, True)] / fine[(5, True)] > 3
     assert fine[(5, False)] > 1.1 * fine[(5, True)]
     c.close()
+
+
+def _interior_leaf_mask(coords, leaf, N):
+    """Cells of leaf blocks whose 6 neighbours lie in leaf blocks of the same level."""
+    idx = {tuple(v): i for i, v in enumerate(np.asarray(coords).tolist())}
+    m = np.zeros((len(coords), N, N, N), dtype=bool)
+    for b, cc in enumerate(np.asarray(coords).tolist()):
+        if not leaf[b]:
+            continue
+        ok = np.ones((N, N, N), dtype=bool)
+        for a in range(3):
+            for s in (-1, 1):
+                nb = list(cc)
+                nb[a] += s
+                j = idx.get(tuple(nb))
+                if j is None or not leaf[j]:
+                    sl = [slice(None)] * 3
+                    sl[a] = slice(N - 1, N) if s == 1 else slice(0, 1)
+                    ok[tuple(sl)] = False
+        m[b] = ok
+    return m
+
+
+def test_vortex_ring_relaxed_criterion_alpha_one_eighth():
+    """Sec. 3.1's second added-levels study (Fig. convergence_w8): with the
+    relaxed criterion alpha = 1/8 fewer blocks are refined, so more source stays
+    on coarse levels and the finest-level error saturates earlier than with
+    alpha = 1/32; and the 7-point Laplacian of the computed field recovers the
+    source only with the source correction, without which the mismatch grows
+    with the number of levels (Fig. offset_target_convergence_w8)."""
+    c = F.Context(N=8, n_interp=6, precision="fp64")
+    fine, lap, nblk = {}, {}, {}
+    for alpha in (1.0 / 8, 1.0 / 32):
+        for L in (3, 4, 5):
+            p, psi = config_vortex_ring(L, 8, 4, 0, alpha=alpha)
+            nblk[(alpha, L)] = sum(len(x) for x in p.coords)
+            leaf = p.leaf_masks()
+            scale = max(np.max(np.abs(psi[l][leaf[l]])) for l in range(L))
+            wmax = max(np.max(np.abs(f)) for f in p.f)
+            for corr in (True, False):
+                bs = F.BlockSet(c, [p.coords], [p.h0])
+                if not corr:
+                    bs.set_option(F.OPT_CORRECTION, 0)
+                for l, f in enumerate(p.f):
+                    bs.load_source(0, l, torch.as_tensor(f))
+                bs.solve()
+                u = [bs.potential(0, l) for l in range(L)]
+                fine[(alpha, L, corr)] = float(np.max(np.abs(u[L - 1].double().cpu().numpy()[leaf[L - 1]]
+                                                            - psi[L - 1][leaf[L - 1]]))) / scale
+                worst = 0.0
+                for l in range(L):
+                    m = _interior_leaf_mask(p.coords[l], leaf[l], 8)
+                    if m.any():
+                        d = bs.laplacian(0, l, u[l]).cpu().numpy() - p.f[l]
+                        worst = max(worst, float(np.max(np.abs(d[m]))) / wmax)
+                lap[(alpha, L, corr)] = worst
+                bs.close()
+    print("blocks", nblk)
+    print("finest-level error", {k: f"{v:.3e}" for k, v in fine.items()})
+    print("max |L_Q Psi_h - omega| / max|omega|", {k: f"{v:.3e}" for k, v in lap.items()})
+    a8, a32 = 1.0 / 8, 1.0 / 32
+    assert all(nblk[(a8, L)] <= nblk[(a32, L)] for L in (3, 4, 5)) and nblk[(a8, 5)] < nblk[(a32, 5)]
+    # saturation: the relaxed criterion gains less from the fifth level
+    assert fine[(a8, 4, True)] / fine[(a8, 5, True)] < fine[(a32, 4, True)] / fine[(a32, 5, True)]
+    for alpha in (a8, a32):
+        # consistency of the forward Laplacian with its inverse needs the correction
+        for L in (4, 5):
+            assert lap[(alpha, L, True)] < lap[(alpha, L, False)], (alpha, L)
+        assert lap[(alpha, 5, False)] > lap[(alpha, 3, False)], alpha
+    c.close()
