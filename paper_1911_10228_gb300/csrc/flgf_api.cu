@@ -160,6 +160,7 @@ struct PhaseOff {  // arena offsets and counts of one phase's launch lists
   int n_fl = 0, fl_max_cells = 0, fl_max_parents = 0;
   size_t fl_groups = 0, fl_rows = 0, fl_dlms = 0, fl_tgt = 0, fl_cells = 0;
   int fl_ncomp = 1, fl_cstride = 0;  // components sharing the frequency-lane groups, their column stride
+  bool fl_split = false;              // rows nearly all full: the two-path product form
   int n_fll = 0; size_t fll_groups = 0, fll_tgt = 0, fll_beg = 0, fll_len = 0, fll_ent = 0;
   int n_inv = 0, n_inv0 = 0; size_t inv_sid = 0, inv_gid = 0, inv_scale = 0;  // finest octree level first (n_inv0)
   std::vector<int> n_itp; std::vector<size_t> itp_ch, itp_par, itp_cpos;
@@ -711,6 +712,16 @@ static void build_fmm(flgf_blockset* bs, Arena& ar, int l, const std::vector<con
       pack_parent_groups(k, dpool[k], nchunk, had_kernel_units(ctx->prec == FLGF_FP64), hl, ctx->order_by_list);
   }
   ph.n_fl = (int)fll.groups.size();
+  {
+    size_t rows = 0, full = 0;
+    for (const FlGroup& g : fll.groups)
+      for (int m = 0; m < g.nact; ++m) {
+        const int n = fll.rows[(size_t)(g.row_off + m) * kFlRowStride];
+        rows += n;
+        for (int j = 0; j < n; ++j) full += fll.dlms[(size_t)(g.row_off + m) * kFlDelta + j] >> 31;
+      }
+    ph.fl_split = rows > 0 && (double)full >= kFlSplitFullFraction * (double)rows;
+  }
   ph.fl_ncomp = vcomp;
   ph.fl_cstride = ph.nblocks / vcomp;
   ph.fl_max_cells = fll.max_cells;
@@ -1460,7 +1471,7 @@ cudaError_t enqueue_fmm(flgf_blockset* bs, const Arena& ar, const PhaseOff& ph, 
     KRUN(ph.n_fl, launch_hadamard_fl(N, ar.at<FlGroup>(ph.fl_groups), ph.n_fl, ph.fl_max_cells, ph.fl_max_parents,
                                      ar.at<uint16_t>(ph.fl_rows), ar.at<uint32_t>(ph.fl_dlms), ar.at<int>(ph.fl_tgt),
                                      ar.at<int>(ph.fl_cells), bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride,
-                                     ph.fl_ncomp, ph.fl_cstride, s));
+                                     ph.fl_ncomp, ph.fl_cstride, ph.fl_split, s));
     KRUN(ph.n_fll, launch_hadamard_fll(N, ar.at<FllGroup>(ph.fll_groups), ph.n_fll, ar.at<int>(ph.fll_tgt),
                                        ar.at<int>(ph.fll_beg), ar.at<int>(ph.fll_len), ar.at<uint32_t>(ph.fll_ent),
                                        bs->spec, bs->acc, ph.nblocks, c->d_kspec, c->kstride, s));

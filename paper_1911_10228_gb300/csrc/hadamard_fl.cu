@@ -33,11 +33,15 @@
 // an absent target's accumulator is never stored, so those products change
 // nothing -- and a delta outside it is skipped by one warp-uniform branch.
 // One straight-line path per delta keeps the unrolled code small (it stays
-// in the instruction cache) and free of per-pair branches.  Rows whose mask
-// holds every delta (bit 31 set by the host; near deltas of a coarse level,
-// whose kernel spectra are zero, count as held) run all 27 deltas as one
-// straight-line block, so that the kernel reads are scheduled ahead of the
-// products.
+// in the instruction cache) and free of per-pair branches; the kernel read of
+// the next delta is issued before the products of the current one.  Rows
+// whose mask holds every delta (bit 31 set by the host; near deltas of a
+// coarse level, whose kernel spectra are zero, count as held) need no tests at
+// all: in phases where at least 90 % of the rows are full, the kernel runs
+// those rows as one straight-line block (the two-path form, faster there),
+// while phases with rows of both kinds keep the single path, whose code stays
+// within the instruction cache.  Both forms compute the same products in the
+// same order.
 #include <algorithm>
 #include <unordered_map>
 #include <vector>
@@ -96,6 +100,32 @@ __device__ __forceinline__ void load_cell(const int* cid, const float2* __restri
 
 // The products of one (parent, cell): kernel offset d = (a - b) - 2e; Kc
 // points at d = -2e, dlm is the row's delta mask.
+// One path for every row: delta dl runs its pairs when its mask bit is set
+// (every bit on full rows), and the kernel read of the next delta is issued,
+// unconditionally, before the products of the current one, so that its
+// shared-memory latency overlaps them.
+__device__ __forceinline__ void cell_products_single(const float4* __restrict__ Kc, uint32_t dlm, const float4 (&f)[8],
+                                                     float (&ar)[8][2], float (&ai)[8][2]) {
+  if (dlm >> 31) dlm = (1u << 27) - 1;
+  float4 kn = Kc[(-49 - 7 - 1) * (kFlFreq / 2)];
+#pragma unroll
+  for (int dl = 0; dl < 27; ++dl) {
+    const float4 k = kn;
+    if (dl + 1 < 27) {
+      const int m0 = (dl + 1) / 9 - 1, m1 = ((dl + 1) / 3) % 3 - 1, m2 = (dl + 1) % 3 - 1;
+      kn = Kc[(m0 * 49 + m1 * 7 + m2) * (kFlFreq / 2)];
+    }
+    if (!((dlm >> dl) & 1u)) continue;
+    const int l0 = dl / 9 - 1, l1 = (dl / 3) % 3 - 1, l2 = dl % 3 - 1;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int b0 = (a >> 2) - l0, b1 = ((a >> 1) & 1) - l1, b2 = (a & 1) - l2;
+      if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b2 < 0 || b2 > 1) continue;  // compile time
+      cmac(ar[a], ai[a], k, f[(b0 << 2) | (b1 << 1) | b2]);
+    }
+  }
+}
+
 template <bool kAll>
 __device__ __forceinline__ void cell_products_m(const float4* __restrict__ Kc, uint32_t dlm, const float4 (&f)[8],
                                                 float (&ar)[8][2], float (&ai)[8][2]) {
@@ -112,12 +142,24 @@ __device__ __forceinline__ void cell_products_m(const float4* __restrict__ Kc, u
     }
   }
 }
-__device__ __forceinline__ void cell_products(const float4* __restrict__ Kc, uint32_t dlm, const float4 (&f)[8],
+__device__ __forceinline__ void cell_products_split(const float4* __restrict__ Kc, uint32_t dlm, const float4 (&f)[8],
                                               float (&ar)[8][2], float (&ai)[8][2]) {
   if (dlm >> 31)
     cell_products_m<true>(Kc, dlm, f, ar, ai);
   else
     cell_products_m<false>(Kc, dlm, f, ar, ai);
+}
+
+// kSplit: the two-path form (phases whose rows are nearly all full), else the
+// single path (its code stays within the instruction cache when rows of both
+// kinds alternate).
+template <bool kSplit>
+__device__ __forceinline__ void cell_products(const float4* __restrict__ Kc, uint32_t dlm, const float4 (&f)[8],
+                                              float (&ar)[8][2], float (&ai)[8][2]) {
+  if constexpr (kSplit)
+    cell_products_split(Kc, dlm, f, ar, ai);
+  else
+    cell_products_single(Kc, dlm, f, ar, ai);
 }
 
 __device__ __forceinline__ const float4* kernel_row(const float4* Ks, int w, int lane) {
@@ -130,7 +172,7 @@ __device__ __forceinline__ const float4* kernel_row(const float4* Ks, int w, int
 
 // kVec: a vector block set (ncomp components); the scalar form compiles
 // without the component loop.
-template <bool kVec>
+template <bool kVec, bool kSplit>
 __global__ void __launch_bounds__(kFlThreads, 1)
     hadamard_fl_kernel(const FlGroup* __restrict__ groups, int ngroups, const uint16_t* __restrict__ rows,
                        const uint32_t* __restrict__ dlms, const int* __restrict__ tgt_ids, const int* __restrict__ cells,
@@ -192,10 +234,10 @@ __global__ void __launch_bounds__(kFlThreads, 1)
     if (ncl > 0) load_cell(CI + 8 * (row[1] & 0x7FF), lane_spec, fa);
     for (int j = 0; j < ncl; j += 2) {
       if (j + 1 < ncl) load_cell(CI + 8 * (row[2 + j] & 0x7FF), lane_spec, fb);
-      cell_products(kernel_row(Ks4, row[1 + j], lane), dm[j], fa, ar, ai);
+      cell_products<kSplit>(kernel_row(Ks4, row[1 + j], lane), dm[j], fa, ar, ai);
       if (j + 1 >= ncl) break;
       if (j + 2 < ncl) load_cell(CI + 8 * (row[3 + j] & 0x7FF), lane_spec, fa);
-      cell_products(kernel_row(Ks4, row[2 + j], lane), dm[j + 1], fb, ar, ai);
+      cell_products<kSplit>(kernel_row(Ks4, row[2 + j], lane), dm[j + 1], fb, ar, ai);
     }
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -331,13 +373,14 @@ size_t fl_smem_bytes(int max_cells, int max_parents) {
 cudaError_t launch_hadamard_fl(int N, const FlGroup* groups, int ngroups, int max_cells, int max_parents,
                                const uint16_t* rows, const uint32_t* dlms, const int* tgt_ids, const int* cells,
                                const void* spec, void* acc, int spec_blocks, const void* kspec,
-                               size_t kspec_level_stride, int ncomp, int cstride, cudaStream_t s) {
+                               size_t kspec_level_stride, int ncomp, int cstride, bool split, cudaStream_t s) {
   if (ngroups <= 0) return cudaSuccess;
   if (ncomp < 1) return cudaErrorInvalidValue;
   const int nfb = nfreq(N) / kFlFreq;
   const size_t sm = fl_smem_bytes(max_cells, max_parents);
   if (sm > kFlSmemBytes || (size_t)nfb * ngroups >= (1u << 31)) return cudaErrorInvalidConfiguration;
-  auto kern = ncomp > 1 ? hadamard_fl_kernel<true> : hadamard_fl_kernel<false>;
+  auto kern = ncomp > 1 ? (split ? hadamard_fl_kernel<true, true> : hadamard_fl_kernel<true, false>)
+                        : (split ? hadamard_fl_kernel<false, true> : hadamard_fl_kernel<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)(nfb * ngroups), kFlThreads, sm, s>>>(

@@ -170,7 +170,9 @@ size_t fl_smem_bytes(int max_cells, int max_parents);
 cudaError_t launch_hadamard_fl(int N, const FlGroup* groups, int ngroups, int max_cells, int max_parents,
                                const uint16_t* rows, const uint32_t* dlms, const int* tgt_ids, const int* cells,
                                const void* spec, void* acc, int spec_blocks, const void* kspec,
-                               size_t kspec_level_stride, int ncomp, int cstride, cudaStream_t s);
+                               size_t kspec_level_stride, int ncomp, int cstride, bool split, cudaStream_t s);
+// Full rows at or above this fraction of a phase's rows: the two-path product form.
+constexpr double kFlSplitFullFraction = 0.9;
 // FP32 frequency-lane pair lists (hadamard_fl.cu), for the targets of sparse
 // tiles: a CTA takes a group of at most kFllTargets targets and a block of
 // kFllFreq consecutive frequencies, a warp one target at a time, a lane one

@@ -305,16 +305,23 @@ __global__ void __launch_bounds__(N * N) interp_add_kernel(const double* __restr
   }
 }
 
+// Block copies (or zero fills) in 16-byte vectors: a block is N^3 values
+// (a multiple of 16 bytes) at a 16-byte aligned offset of its array.
 template <typename R>
 __global__ void copy_blocks_kernel(int N, const R* __restrict__ src, const int* __restrict__ src_ids,
                                    R* __restrict__ dst, const int* __restrict__ dst_ids,
                                    const uint8_t* __restrict__ zero) {
   const int N3 = N * N * N;
+  const int nv = N3 * (int)sizeof(R) / 16;
   const int i = blockIdx.x;
   const bool z = zero != nullptr && zero[i];
-  const R* s = src + (size_t)src_ids[i] * N3;
-  R* d = dst + (size_t)dst_ids[i] * N3;
-  for (int e = threadIdx.x; e < N3; e += blockDim.x) d[e] = z ? R(0) : s[e];
+  int4* d = reinterpret_cast<int4*>(dst + (size_t)dst_ids[i] * N3);
+  if (z) {
+    for (int e = threadIdx.x; e < nv; e += blockDim.x) d[e] = make_int4(0, 0, 0, 0);
+  } else {
+    const int4* s = reinterpret_cast<const int4*>(src + (size_t)src_ids[i] * N3);
+    for (int e = threadIdx.x; e < nv; e += blockDim.x) d[e] = __ldg(s + e);
+  }
 }
 
 template <typename R>
