@@ -22,8 +22,8 @@ import torch
 from .flgf import BlockSet, Context, OPT_GRAPH
 
 DEFAULT_CANDIDATES = [
-    (30, (4, 4, 8)), (0, (4, 4, 8)), (15, (4, 4, 8)), (50, (4, 4, 8)),
-    (30, (4, 4, 4)), (15, (4, 4, 4)), (50, (4, 4, 4)), (30, (2, 4, 8)),
+    (30, (4, 4, 8)), (0, (4, 4, 8)), (15, (4, 4, 8)), (40, (4, 4, 8)), (50, (4, 4, 8)),
+    (30, (4, 4, 4)), (50, (4, 4, 4)), (30, (2, 4, 8)),
 ]
 
 
