@@ -1,6 +1,6 @@
 // Internal launcher interface between the host orchestration (flgf_api.cu)
-// and the kernels (lgf.cu, fft.cu, hadamard.cu, stencil.cu).  Not part of the
-// public C ABI.
+// and the kernels (lgf.cu, fft.cu, hadamard.cu, hadamard_fl.cu, stencil.cu,
+// meshgen.cu, flgf_static.cu).  Not part of the public C ABI.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -232,3 +232,23 @@ def test_per_parent_anterpolation_equals_cluster_form():
     bs.solve()
     for i in range(len(probs)):
         assert torch.equal(bs.potential(i, 0).cpu(), singles[i]), i
+
+
+def test_mac_product_forms_agree_bit_for_bit():
+    """The FP32 frequency-lane MAC runs a phase in its two-path form when at
+    least 90 % of the phase's rows are full, in the single-path form otherwise;
+    both compute the same products in the same order.  A small uniform box
+    alone (every row full: two-path form) and the same box in one block set
+    with a sparse problem (mostly masked rows: single path) give the same
+    potential bit for bit."""
+    from paper_1911_10228_gb300.inputs import random_sparse_problem
+    box = _gauss_problem(box_coords(4), 8, 3)
+    sparse = random_sparse_problem(11, N=8, nblk_range=(600, 900), max_levels=1)
+    c = ctx(8, "fp32")
+    alone = F.solve_problem(c, box)[0].cpu()
+    bs = F.BlockSet(c, [box.coords, sparse.coords], [box.h0, sparse.h0])
+    bs.load_source(0, 0, torch.as_tensor(box.f[0]))
+    bs.load_source(1, 0, torch.as_tensor(sparse.f[0]))
+    bs.solve()
+    assert torch.equal(bs.potential(0, 0).cpu(), alone)
+    bs.close()
