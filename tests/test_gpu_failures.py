@@ -136,7 +136,11 @@ def test_fp64_adjoint_repeats_to_round_off():
         bs.solve_adjoint()
         runs.append([bs.gradient(0, l).cpu().numpy() for l in range(p.n_levels)])
     scale = max(np.max(np.abs(x)) for x in runs[0])
+    # a coarse cell sums up to ~64 fine contributions; reordering a sum of M
+    # terms moves it by at most about M eps sum|terms|, a few times 64 * 1.1e-16
+    # of the scale (measured up to 1.06e-14); a race or a lost update would be
+    # orders of magnitude larger
     for a, b in zip(*runs):
-        assert np.max(np.abs(a - b)) <= 1e-14 * scale
+        assert np.max(np.abs(a - b)) <= 1e-13 * scale
     bs.close()
     ctx.close()
