@@ -138,19 +138,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def file_sha(path):
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def files_sha(paths):
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_src: str, kernel: str, workload: str):
     """DRAM bytes per step (all launches of one solve) of a kernel from the
-    committed ncu summary, if it was taken on the current kernel source (else
-    None)."""
+    committed ncu summary, if it was taken on the current kernel source and
+    the launch constants of internal.h (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    sha = file_sha(os.path.join(ROOT, "paper_1911_10228_gb300", "csrc", kernel_src))
+    csrc = os.path.join(ROOT, "paper_1911_10228_gb300", "csrc")
+    sha = files_sha([os.path.join(csrc, kernel_src), os.path.join(csrc, "internal.h")])
     with open(path) as f:
         for line in f:
             if line.startswith("#") or not line.strip():

@@ -140,7 +140,7 @@ cudaError_t launch_hadamard_list(int N, const ListGroup* groups, int ngroups, in
 // ((l0 + 1) * 3 + l1 + 1) * 3 + l2 + 1 set when a target-source child pair
 // with a - b = l contributes, bit 31 when all 27 may run (fl_delta_mask).
 constexpr int kFlWarps = 16;
-constexpr int kFlMaxParents = 64;
+constexpr int kFlMaxParents = 128;
 constexpr int kFlMaxCells = 768;
 constexpr int kFlFreq = 64;
 constexpr int kFlRowStride = 28;
