@@ -105,7 +105,7 @@ void flgf_destroy(flgf_ctx* ctx);
  *                      into the dense kernel's groups.
  *   FLGF_CTX_MAC       FP32 contexts: the kernels of the spectrum MAC.
  *                      1 (default): dense tiles with one target parent per
- *                      warp and one or two frequencies per thread (absent
+ *                      warp and two frequencies per thread (absent
  *                      cells and children are skipped warp-uniformly), sparse
  *                      tiles (FLGF_CTX_LIST_PCT) as pair lists with one target
  *                      per warp and one frequency per thread; 2: the same
