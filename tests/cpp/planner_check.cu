@@ -191,6 +191,20 @@ int main(int argc, char** argv) {
         }
       }
     }
+    // the product form of the phase: the two-path form exactly when at least
+    // kFlSplitFullFraction of its rows are full
+    {
+      long rows = 0, full = 0;
+      for (int gi = 0; gi < ph.n_fl; ++gi) {
+        const FlGroup& g = FG[gi];
+        for (int m = 0; m < g.nact; ++m) {
+          const int n = frows[(size_t)(g.row_off + m) * kFlRowStride];
+          rows += n;
+          for (int j = 0; j < n; ++j) full += fdlm[(size_t)(g.row_off + m) * kFlDelta + j] >> 31;
+        }
+      }
+      bad += ph.fl_split != (rows > 0 && (double)full >= kFlSplitFullFraction * (double)rows);
+    }
     // frequency-lane pair lists
     const FllGroup* QG = reinterpret_cast<const FllGroup*>(base + ph.fll_groups);
     const int* qt = reinterpret_cast<const int*>(base + ph.fll_tgt);
